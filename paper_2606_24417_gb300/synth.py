@@ -1,0 +1,278 @@
+"""Seeded synthetic genomic workloads (inputs only).
+
+This module generates DNA sequences, read sets and request streams.  It holds
+none of the filter's arithmetic: its random numbers come from a counter-based
+generator built on the MurmurHash3 64-bit finaliser (Appleby), and reverse
+strands are produced with a byte translation table.  Everything is
+deterministic for a given seed and independent of the numpy version.
+
+Workload shapes follow the filter's evaluation: uniform random DNA, Markov
+genomes with a GC target and repeat copies (bacterial- and human-shaped),
+reads sampled from either strand with substitution errors, uniform random
+reads, lognormal read lengths and Poisson request arrivals.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_ACGT = np.frombuffer(b"ACGT", dtype=np.uint8)
+_COMPLEMENT = np.arange(256, dtype=np.uint8)
+for _a, _b in zip(b"ACGTacgt", b"TGCAtgca"):
+    _COMPLEMENT[_a] = _b
+
+_M1 = np.uint64(0xFF51AFD7ED558CCD)
+_M2 = np.uint64(0xC4CEB9FE1A85EC53)
+_S33 = np.uint64(33)
+
+
+def _fmix64(x: np.ndarray) -> np.ndarray:
+    x = x ^ (x >> _S33)
+    x = x * _M1
+    x = x ^ (x >> _S33)
+    x = x * _M2
+    return x ^ (x >> _S33)
+
+
+def _stream_key(seed: int, stream: int) -> np.uint64:
+    with np.errstate(over="ignore"):
+        a = _fmix64(np.array([seed & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64))
+        b = _fmix64(a ^ np.uint64(stream & 0xFFFFFFFFFFFFFFFF) ^ np.uint64(0x632BE59BD9B4E019))
+    return b[0]
+
+
+def u64(seed: int, stream: int, start: int, n: int) -> np.ndarray:
+    """n counter-based 64-bit random words: element i depends only on (seed, stream, start+i)."""
+    key = _stream_key(seed, stream)
+    idx = np.arange(start, start + n, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return _fmix64(idx * np.uint64(0xD6E8FEB86659FD93) + key)
+
+
+def uniform01(seed: int, stream: int, start: int, n: int) -> np.ndarray:
+    """Uniform doubles in [0, 1) (53 bits)."""
+    return (u64(seed, stream, start, n) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
+def randint(seed: int, stream: int, n: int, lo: int, hi: int) -> np.ndarray:
+    """Integers uniform in [lo, hi) (multiply-shift on 53-bit uniforms)."""
+    span = hi - lo
+    return lo + np.floor(uniform01(seed, stream, 0, n) * span).astype(np.int64)
+
+
+# ----------------------------------------------------------------------------
+# sequences
+# ----------------------------------------------------------------------------
+def uniform_dna(n: int, seed: int) -> np.ndarray:
+    """n uniform random bases (uint8 ASCII 'ACGT')."""
+    out = np.empty(n, dtype=np.uint8)
+    chunk = 1 << 24
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        w = u64(seed, 1, s // 32, (e - s + 31) // 32)
+        two = np.empty((w.size, 32), dtype=np.uint8)
+        for j in range(32):
+            two[:, j] = ((w >> np.uint64(2 * j)) & np.uint64(3)).astype(np.uint8)
+        out[s:e] = _ACGT[two.reshape(-1)[: e - s]]
+    return out
+
+
+def reverse_complement(x: np.ndarray) -> np.ndarray:
+    """Reverse strand of an ASCII DNA array (non-ACGT bytes kept)."""
+    return _COMPLEMENT[np.asarray(x, dtype=np.uint8)[::-1]]
+
+
+def _markov_table(order: int, gc: float, seed: int) -> np.ndarray:
+    """Transition table [4^order, 4]: Dirichlet(1) rows tilted to a stationary GC."""
+    n_ctx = 4 ** order
+    e = -np.log1p(-uniform01(seed, 7, 0, n_ctx * 4)).reshape(n_ctx, 4)
+    base = e / e.sum(axis=1, keepdims=True)
+    is_gc = np.array([0.0, 1.0, 1.0, 0.0])
+
+    def tilt(t):
+        w = base * np.where(is_gc > 0, t, 1.0)[None, :]
+        return w / w.sum(axis=1, keepdims=True)
+
+    def stationary_gc(P):
+        # power iteration on the 4^order context chain
+        pi = np.full(n_ctx, 1.0 / n_ctx)
+        nxt = (np.arange(n_ctx)[:, None] * 4 + np.arange(4)[None, :]) % n_ctx
+        for _ in range(200):
+            new = np.zeros(n_ctx)
+            np.add.at(new, nxt.reshape(-1), (pi[:, None] * P).reshape(-1))
+            pi = new
+        return float((pi[:, None] * P * is_gc[None, :]).sum())
+
+    lo, hi = 1e-3, 1e3
+    for _ in range(60):  # bisection on the log of the tilt
+        mid = math.sqrt(lo * hi)
+        if stationary_gc(tilt(mid)) < gc:
+            lo = mid
+        else:
+            hi = mid
+    return tilt(math.sqrt(lo * hi))
+
+
+def markov_dna(n: int, order: int, gc: float, seed: int, n_chains: int = 4096) -> np.ndarray:
+    """Order-`order` Markov DNA of length n, run as n_chains independent
+    segments (vectorised across segments) that are concatenated."""
+    P = _markov_table(order, gc, seed)
+    cum = np.cumsum(P, axis=1)
+    cum[:, -1] = 1.0
+    n_ctx = 4 ** order
+    n_chains = max(1, min(n_chains, n))
+    seg = (n + n_chains - 1) // n_chains
+    codes = np.empty((n_chains, seg), dtype=np.uint8)
+    ctx = randint(seed, 11, n_chains, 0, n_ctx)
+    for t in range(seg):
+        u = uniform01(seed, 12, t * n_chains, n_chains)
+        c = (u[:, None] >= cum[ctx]).sum(axis=1).astype(np.int64)
+        codes[:, t] = c
+        ctx = (ctx * 4 + c) % n_ctx
+    return _ACGT[codes.reshape(-1)[:n]]
+
+
+def gc_fraction(x: np.ndarray) -> float:
+    x = np.asarray(x, dtype=np.uint8)
+    return float(np.isin(x, np.frombuffer(b"CGcg", dtype=np.uint8)).mean())
+
+
+def add_exact_repeats(genome: np.ndarray, frac: float, min_len: int, max_len: int,
+                      seed: int) -> np.ndarray:
+    """Overwrite about frac of the genome with exact copies of other segments
+    (uniform length in [min_len, max_len], uniform source/destination,
+    random strand)."""
+    g = genome.copy()
+    n = g.size
+    if n <= max_len * 2:
+        return g
+    mean = (min_len + max_len) / 2
+    count = int(round(frac * n / mean))
+    lens = randint(seed, 21, count, min_len, max_len + 1)
+    src = randint(seed, 22, count, 0, n - max_len)
+    dst = randint(seed, 23, count, 0, n - max_len)
+    strand = randint(seed, 24, count, 0, 2)
+    for L, a, b, st in zip(lens, src, dst, strand):
+        piece = genome[a:a + L]
+        g[b:b + L] = reverse_complement(piece) if st else piece
+    return g
+
+
+def add_diverged_repeats(genome: np.ndarray, frac: float, n_families: int, min_len: int,
+                         max_len: int, divergence: float, seed: int, order: int = 5,
+                         gc: float = 0.41) -> np.ndarray:
+    """Interspersed repeats: n_families consensus sequences (log-uniform lengths,
+    drawn from the same Markov chain), copied with independent substitutions
+    and random strand until about frac of the genome is covered."""
+    g = genome.copy()
+    n = g.size
+    ll = np.exp(np.log(min_len) + uniform01(seed, 31, 0, n_families)
+                * (np.log(max_len) - np.log(min_len)))
+    flen = np.maximum(min_len, ll.astype(np.int64))
+    fam_src = markov_dna(int(flen.sum()), order, gc, seed + 1, n_chains=min(4096, n_families))
+    starts = np.concatenate([[0], np.cumsum(flen)[:-1]])
+    mean = float(flen.mean())
+    count = int(round(frac * n / mean))
+    fam = randint(seed, 32, count, 0, n_families)
+    dst = randint(seed, 33, count, 0, max(1, n - max_len))
+    strand = randint(seed, 34, count, 0, 2)
+    pos_ctr = 0
+    for f, b, st in zip(fam, dst, strand):
+        L = int(flen[f])
+        piece = fam_src[starts[f]:starts[f] + L].copy()
+        u = uniform01(seed, 35, pos_ctr, L)
+        sub = randint(seed + pos_ctr, 36, L, 1, 4)
+        pos_ctr += L
+        hit = u < divergence
+        if hit.any():
+            code = np.searchsorted(_ACGT, piece[hit])
+            piece[hit] = _ACGT[(code + sub[hit]) % 4]
+        if st:
+            piece = reverse_complement(piece)
+        g[b:b + L] = piece
+    return g
+
+
+# ----------------------------------------------------------------------------
+# reads
+# ----------------------------------------------------------------------------
+def concat(reads) -> tuple[np.ndarray, np.ndarray]:
+    """Concatenate a list of uint8 reads into (seq, off[n+1])."""
+    lens = np.array([len(r) for r in reads], dtype=np.uint64)
+    off = np.zeros(len(reads) + 1, dtype=np.uint64)
+    np.cumsum(lens, out=off[1:])
+    seq = np.concatenate([np.asarray(r, dtype=np.uint8) for r in reads]) if reads else \
+        np.zeros(0, dtype=np.uint8)
+    return seq, off
+
+
+def fixed_length_offsets(n_reads: int, length: int) -> np.ndarray:
+    return (np.arange(n_reads + 1, dtype=np.uint64) * np.uint64(length))
+
+
+def sample_reads(genome: np.ndarray, n_reads: int, length: int, error_rate: float,
+                 seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """n_reads reads of one length from uniform positions on a random strand,
+    each base substituted with probability error_rate (uniform among the
+    other three).  Returns (seq, off)."""
+    n = genome.size
+    starts = randint(seed, 41, n_reads, 0, n - length + 1)
+    idx = starts[:, None] + np.arange(length)[None, :]
+    reads = genome[idx]
+    strand = randint(seed, 42, n_reads, 0, 2).astype(bool)
+    if strand.any():
+        reads[strand] = _COMPLEMENT[reads[strand][:, ::-1]]
+    flat = reads.reshape(-1)
+    u = uniform01(seed, 43, 0, flat.size)
+    hit = u < error_rate
+    if hit.any():
+        sub = randint(seed, 44, int(hit.sum()), 1, 4)
+        code = np.searchsorted(_ACGT, flat[hit])
+        flat[hit] = _ACGT[(code + sub) % 4]
+    return flat, fixed_length_offsets(n_reads, length)
+
+
+def random_reads(n_reads: int, length: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    return uniform_dna(n_reads * length, seed), fixed_length_offsets(n_reads, length)
+
+
+def lognormal_lengths(n: int, median: float, sigma: float, lo: int, hi: int,
+                      seed: int) -> np.ndarray:
+    """clip(round(lognormal(ln median, sigma)), lo, hi) via Box-Muller."""
+    u1 = uniform01(seed, 51, 0, n)
+    u2 = uniform01(seed, 52, 0, n)
+    z = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+    return np.clip(np.rint(np.exp(np.log(median) + sigma * z)), lo, hi).astype(np.int64)
+
+
+def poisson_arrivals(n: int, rate_per_s: float, seed: int) -> np.ndarray:
+    """Arrival times (s) of a Poisson process."""
+    gaps = -np.log1p(-uniform01(seed, 61, 0, n)) / rate_per_s
+    return np.cumsum(gaps)
+
+
+# ----------------------------------------------------------------------------
+# the evaluation workloads
+# ----------------------------------------------------------------------------
+def bacterial_genome(n: int = 100_000_000, seed: int = 2) -> np.ndarray:
+    """Order-3 Markov genome at GC 50% with 3% of it overwritten by exact
+    1-10 kb repeat copies (random strand)."""
+    g = markov_dna(n, 3, 0.5, seed)
+    return add_exact_repeats(g, 0.03, 1000, 10000, seed + 100)
+
+
+def human_like_genome(n: int = 3_100_000_000, seed: int = 5) -> np.ndarray:
+    """Order-5 Markov genome at GC 41% with 45% covered by interspersed copies
+    of 500 repeat families (300 bp - 6 kb, 10% divergence, random strand)."""
+    g = markov_dna(n, 5, 0.41, seed, n_chains=65536)
+    return add_diverged_repeats(g, 0.45, 500, 300, 6000, 0.10, seed + 100)
+
+
+def mixed_query_reads(genome: np.ndarray, n_sampled: int, n_random: int, length: int,
+                      error_rate: float, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """n_sampled reads from the genome (with errors) followed by n_random uniform reads."""
+    s1, _ = sample_reads(genome, n_sampled, length, error_rate, seed)
+    s2, _ = random_reads(n_random, length, seed + 1)
+    seq = np.concatenate([s1, s2])
+    return seq, fixed_length_offsets(n_sampled + n_random, length)

@@ -1,0 +1,111 @@
+"""A second, string-level Super Bloom filter for tiny inputs (tests only).
+
+It works on Python strings and integers and shares nothing with the C oracle:
+k-mers, m-mers and s-mers are substrings, reverse complements come from
+str.translate + reversal, values from base-4 digit strings.  The filter is
+rebuilt from the SET of (shard, canonical s-mer) pairs that the inserted
+k-mers produce, so it also checks that the oracle's bit array is exactly the
+union of the pairs' bits (order- and multiplicity-free, Sec. II-B / Alg. 1).
+"""
+from __future__ import annotations
+
+_DIGIT = str.maketrans("ACGTacgt", "01230123")
+_RC = str.maketrans("ACGTacgt", "TGCAtgca")
+_M64 = (1 << 64) - 1
+
+
+def value(x: str) -> int:
+    return int(x.translate(_DIGIT), 4) if x else 0
+
+
+def revcomp(x: str) -> str:
+    return x.translate(_RC)[::-1]
+
+
+def mix64(x: int) -> int:
+    x ^= x >> 30
+    x = (x * 0xBF58476D1CE4E5B9) & _M64
+    x ^= x >> 27
+    x = (x * 0x94D049BB133111EB) & _M64
+    x ^= x >> 31
+    return x
+
+
+class BruteSBF:
+    def __init__(self, k, m, s, H, bits, shard_bits=512, canonical=True):
+        self.k, self.m, self.s, self.H, self.B = k, m, s, H, shard_bits
+        self.canonical = canonical
+        self.N = -(-bits // shard_bits)
+        self.pairs = set()
+
+    def canon(self, x: str) -> int:
+        v = value(x)
+        return min(v, value(revcomp(x))) if self.canonical else v
+
+    def key(self, v: int) -> int:
+        if 2 * self.m <= 32:
+            return (v * 0x9E3779B9) % (1 << 32)
+        return (v * 0x9E3779B97F4A7C15) % (1 << 64)
+
+    def minimizer(self, kmer: str) -> int:
+        mmers = [self.canon(kmer[i:i + self.m]) for i in range(self.k - self.m + 1)]
+        return min(mmers, key=self.key)
+
+    def shard(self, kmer: str) -> int:
+        return (mix64(self.minimizer(kmer) ^ 0x14057B7EF767814F) * self.N) >> 64
+
+    def smers(self, kmer: str):
+        return [self.canon(kmer[t:t + self.s]) for t in range(self.k - self.s + 1)]
+
+    def bit_positions(self, x: int, v: int):
+        """Absolute bit indices of canonical s-mer v in shard x."""
+        h = mix64(v ^ 0x5851F42D4C957F2D)
+        W = self.B // 64
+        S = min(self.H, W)
+        sector_bits = self.B // S
+        b = sector_bits.bit_length() - 1
+        q = 64 // self.H
+        out = []
+        for i in range(self.H):
+            if q >= b:
+                p = (h >> (i * q)) % sector_bits
+            else:
+                p = ((h * ((0x9E3779B97F4A7C15 * (2 * i + 1)) & _M64)) & _M64) >> (64 - b)
+            out.append(x * self.B + (i % S) * sector_bits + p)
+        return out
+
+    @staticmethod
+    def kmers_of(read: str, k: int):
+        for p in range(len(read) - k + 1):
+            km = read[p:p + k]
+            if all(ch in "ACGTacgt" for ch in km):
+                yield p, km
+
+    def insert_read(self, read: str):
+        for _, km in self.kmers_of(read, self.k):
+            x = self.shard(km)
+            for v in self.smers(km):
+                self.pairs.add((x, v))
+
+    def bitset(self) -> set:
+        out = set()
+        for x, v in self.pairs:
+            out.update(self.bit_positions(x, v))
+        return out
+
+    def words(self):
+        import numpy as np
+
+        w = np.zeros(self.N * self.B // 64, dtype=np.uint64)
+        for bit in self.bitset():
+            w[bit // 64] |= np.uint64(1 << (bit % 64))
+        return w
+
+    def query_kmer(self, km: str, bitset: set) -> bool:
+        x = self.shard(km)
+        return all(b in bitset for v in self.smers(km) for b in self.bit_positions(x, v))
+
+    def query_kmer_exact(self, km: str) -> bool:
+        """Membership of all of the k-mer's (shard, s-mer) pairs in the inserted set."""
+        x = self.shard(km)
+        return all((x, v) in self.pairs for v in self.smers(km))
