@@ -1,0 +1,419 @@
+"""Benchmark: Super Bloom filter insert + query on the bacterial-genome workload.
+
+One step = clear the 2^30-bit filter, insert a 100 Mbp synthetic genome, then
+query 20M 150 bp reads (10M sampled from the genome with 1% errors, 10M
+random) -- the whole hot path, inputs resident in HBM.  value = (inserted +
+queried k-mer positions) / time.  `e2e` repeats the step through the host
+entry points of the C ABI (pinned host buffers, copies inside the timed
+region).  The CPU oracle runs on a bounded sample as the reported baseline;
+`--impl reference` times the oracle alone (there is no runnable reference
+code for this paper).
+
+Under torchrun each rank builds its own filter replica and queries its own
+20M reads (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "insert/query k-mers/s (k=31,s=28,m=16,H=4), % HBM sector roofline; served p99"
+K, M, S, H = 31, 16, 28, 4
+FILTER_BITS = 1 << 30
+SHARD_BITS = 512
+GENOME_BP = 100_000_000
+N_SAMPLED = 10_000_000
+N_RANDOM = 10_000_000
+READ_LEN = 150
+WORKLOAD = ("bacterial-genome-shaped: insert a 100 Mbp order-3 Markov genome (GC 50%, 3% "
+            "1-10 kb exact repeats) into a 2^30-bit filter of 512-bit shards; query 10M 150 bp "
+            "reads sampled from it (1% substitutions, both strands) + 10M random 150 bp reads")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_workload(rank: int):
+    from paper_2606_24417_gb300 import synth
+
+    t = time.time()
+    genome = synth.bacterial_genome(GENOME_BP, seed=2)
+    reads, roff = synth.mixed_query_reads(genome, N_SAMPLED, N_RANDOM, READ_LEN, 0.01,
+                                          seed=3 + 1000 * rank)
+    log(f"[bench] rank {rank}: workload generated in {time.time() - t:.1f}s")
+    return genome, reads, roff
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2606_24417_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as fh:
+                h.update(fn.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get(kernel)
+    if not e or e.get("source_digest") != kernel_source_digest():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ---------------------------------------------------------------------------
+def cpu_baseline(genome, reads, roff, budget_s: float = 15.0):
+    from oracle import OracleSBF
+
+    def run(n_gen, n_reads):
+        f = OracleSBF(K, M, S, H, FILTER_BITS, shard_bits=SHARD_BITS)
+        g = genome[:n_gen]
+        t = time.perf_counter()
+        f.insert(g, np.array([0, g.size], dtype=np.uint64))
+        q = reads[: n_reads * READ_LEN]
+        qo = roff[: n_reads + 1]
+        f.query(q, qo)
+        dt = time.perf_counter() - t
+        kmers = (g.size - K + 1) + n_reads * (READ_LEN - K + 1)
+        return kmers, dt
+
+    # calibrate on a small sample, then size the sample to the budget;
+    # reads come half from the sampled and half from the random part
+    k0, t0 = run(200_000, 2_000)
+    scale = max(1.0, budget_s / max(t0, 1e-3))
+    n_gen = int(min(GENOME_BP, 200_000 * scale))
+    n_reads = int(min(N_SAMPLED, 2_000 * scale))
+    kmers, dt = run(n_gen, n_reads)
+    return {"value": kmers / dt, "unit": "k-mers/s", "cores": 1, "kind": "oracle",
+            "sample": f"insert the first {n_gen} bp of the genome, then query the first "
+                      f"{n_reads} sampled reads ({kmers} k-mer positions, {dt:.1f} s, "
+                      f"single-threaded C oracle)"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle as it stands
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    genome, reads, roff = make_workload(0)
+    from oracle import OracleSBF
+
+    times, kmers_step = [], 0
+    n_gen, n_reads = 2_000_000, 20_000
+    for i in range(args.warmup + args.steps):
+        f = OracleSBF(K, M, S, H, FILTER_BITS, shard_bits=SHARD_BITS)
+        g = genome[:n_gen]
+        t = time.perf_counter()
+        f.insert(g, np.array([0, g.size], dtype=np.uint64))
+        f.query(reads[: n_reads * READ_LEN], roff[: n_reads + 1])
+        dt = time.perf_counter() - t
+        kmers_step = (n_gen - K + 1) + n_reads * (READ_LEN - K + 1)
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = kmers_step * len(times) / total
+    sample = (f"each step inserts the first {n_gen} bp of the genome and queries the first "
+              f"{n_reads} reads ({kmers_step} k-mer positions) with the single-threaded C oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "k-mers/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "k": K, "m": M, "s": S, "H": H,
+                       "filter_bits": FILTER_BITS, "shard_bits": SHARD_BITS},
+            "cpu_baseline": {"value": value, "unit": "k-mers/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "k-mers/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2606_24417_gb300 import build_lib
+    from paper_2606_24417_gb300.sbf import SuperBloomFilter
+
+    build_lib.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    genome, reads, roff = make_workload(rank)
+    n_reads = roff.size - 1
+    goff = np.array([0, genome.size], dtype=np.uint64)
+    ins_kmers = genome.size - K + 1
+    q_kmers = n_reads * (READ_LEN - K + 1)
+    kmers_step = ins_kmers + q_kmers
+
+    d_genome = torch.from_numpy(genome).to(dev)
+    d_goff = torch.from_numpy(goff.astype(np.int64)).to(dev)
+    d_reads = torch.from_numpy(reads).to(dev)
+    d_roff = torch.from_numpy(roff.astype(np.int64)).to(dev)
+    d_bits = torch.empty((reads.size + 31) // 32, dtype=torch.int32, device=dev)
+    d_hits = torch.empty(n_reads, dtype=torch.int32, device=dev)
+    stats = torch.zeros(3, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    f = SuperBloomFilter(K, M, S, H, FILTER_BITS, shard_bits=SHARD_BITS)
+    stream = torch.cuda.current_stream()
+
+    # super-k-mer runs of the query batch (shard loads the method needs)
+    f.clear()
+    f.insert(d_genome, d_goff)
+    f.query(d_reads, d_roff, bits=d_bits, hits=d_hits, stats=stats)
+    torch.cuda.synchronize()
+    valid_q, runs_q, pos_q = (int(x) for x in stats.cpu().tolist())
+    stats.zero_()
+    f.query(d_genome, d_goff, want_bits=False, want_hits=False, stats=stats)
+    torch.cuda.synchronize()
+    valid_i, runs_i, _ = (int(x) for x in stats.cpu().tolist())
+
+    def step(ev):
+        f.clear()
+        ev[0].record(stream)
+        f.insert(d_genome, d_goff)
+        ev[1].record(stream)
+        f.query(d_reads, d_roff, bits=d_bits, hits=d_hits)
+        ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+    torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    sampler = ClockSampler(local_rank)
+    if rank == 0:
+        sampler.start()
+        time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(1)  # L2 flush between timed steps (outside the events)
+        step(evs[i])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if rank == 0 else None
+    t_ins = [evs[i][0].elapsed_time(evs[i][1]) for i in range(args.steps)]
+    t_q = [evs[i][1].elapsed_time(evs[i][2]) for i in range(args.steps)]
+    total_ms = sum(t_ins) + sum(t_q)
+    if dist:
+        t = torch.tensor([total_ms, sum(t_ins), sum(t_q)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, ins_ms_sum, q_ms_sum = t.tolist()
+    else:
+        ins_ms_sum, q_ms_sum = sum(t_ins), sum(t_q)
+    value = world * kmers_step * args.steps / (total_ms / 1e3)
+
+    # ---- e2e through the host entry points (pinned host buffers) ----------
+    h_genome = torch.from_numpy(genome).pin_memory().numpy()
+    h_goff = goff
+    h_reads = torch.from_numpy(reads).pin_memory().numpy()
+    h_roff = roff
+    h_bits = torch.empty((reads.size + 31) // 32, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+    h_hits = torch.empty(n_reads, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(1):
+        f.clear()
+        f.insert_host(h_genome, h_goff)
+        f.query_host(h_reads, h_roff, h_bits, h_hits)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        f.clear()
+        f.insert_host(h_genome, h_goff)
+        f.query_host(h_reads, h_roff, h_bits, h_hits)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    # e2e answers equal the device-resident answers
+    same = bool(np.array_equal(h_bits, d_bits.cpu().numpy().view(np.uint32)) and
+                np.array_equal(h_hits, d_hits.cpu().numpy().view(np.uint32)))
+    e2e_value = world * kmers_step * e2e_steps / e2e_s
+    h2d = genome.nbytes + goff.nbytes + reads.nbytes + roff.nbytes
+    d2h = h_bits.nbytes + h_hits.nbytes
+
+    if rank != 0:
+        return 0
+
+    # ---- roofline of the dominant kernel (query) --------------------------
+    peak, peak_kind = measured_peaks()
+    q_ms = q_ms_sum / args.steps
+    ins_ms = ins_ms_sum / args.steps
+    # algorithmic bytes per query launch: read bytes + offsets, one shard load
+    # per super-k-mer run, the bit-packed answers and the per-read hits
+    q_bytes = reads.nbytes + roff.nbytes + runs_q * (SHARD_BITS // 8) + (reads.size + 7) // 8 + 4 * n_reads
+    # insert: genome bytes + a read-modify-write of one shard per run
+    i_bytes = genome.nbytes + runs_i * 2 * (SHARD_BITS // 8)
+    dominant = "query" if q_ms >= ins_ms else "insert"
+    d_bytes, d_ms = (q_bytes, q_ms) if dominant == "query" else (i_bytes, ins_ms)
+    achieved = d_bytes / (d_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": profiled_traffic(dominant),
+                "kernel": dominant, "peak_kind": f"{peak_kind} (copy bandwidth)",
+                "algorithmic_bytes_per_launch": d_bytes, "launch_ms": d_ms}
+    cpu = cpu_baseline(genome, reads, roff) if world == 1 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "k-mers/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "k": K, "m": M, "s": S, "H": H,
+                   "filter_bits": FILTER_BITS, "shard_bits": SHARD_BITS,
+                   "insert_kmers": ins_kmers, "query_kmers": q_kmers,
+                   "l2": "inputs larger than L2 (3.0 GB of reads per step) and a 256 MB L2 "
+                         "flush between timed steps"},
+        "insert_kmers_per_s": world * ins_kmers / (ins_ms / 1e3),
+        "query_kmers_per_s": world * q_kmers / (q_ms / 1e3),
+        "insert_ms": ins_ms, "query_ms": q_ms,
+        "runs_per_kmer": {"query": runs_q / max(valid_q, 1), "insert": runs_i / max(valid_i, 1)},
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": "k-mers/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "answers_match_device": same},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("[bench] warmup raised to 3")
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,148 @@
+/*
+ * sbf.h -- C ABI of the GB300 Super Bloom filter library (libsbf.so).
+ *
+ * A Super Bloom filter (SBF; cuSBF paper, Sec. II-B) stores DNA k-mers.  A
+ * k-mer's minimizer (the m-mer of smallest order key among its k-m+1 windows)
+ * picks one shard of shard_bits bits; each of the k-mer's k-s+1 s-mers sets
+ * (insert) or tests (query) H bits inside that shard; a query is positive only
+ * if every one of those (k-s+1)*H bits is set (Findere, Eq. 2).  Shards are
+ * split into min(H, shard_bits/64) sectors and hash i addresses sector
+ * i mod S (Sec. IV-B); bit positions come from slices of a 64-bit s-mer hash
+ * (bit-slicing, Sec. IV-G).  The exact hash functions, the canonical-k-mer
+ * rule and the 512-bit layout are fixed by this library (see the sbf_create
+ * notes below); they are what the parity tests check bit for bit.
+ *
+ * Conventions shared by every call:
+ *  - Sequences are ASCII bytes.  A/C/G/T (either case) are bases; any other
+ *    byte is invalid and no k-mer covering it exists (Sec. IV-C validity,
+ *    Sec. IV-F separators).
+ *  - A batch of reads is one concatenated byte array `seq` of `seq_len` bytes
+ *    and `n_reads + 1` offsets: read r is seq[off[r], off[r+1]).  Offsets are
+ *    non-decreasing, off[0] = 0 and off[n_reads] = seq_len.  K-mers never
+ *    span two reads.  Calls with device offsets cannot check them without a
+ *    synchronisation: offsets outside [0, seq_len] are clamped, so a
+ *    malformed table gives wrong answers but no out-of-bounds access.
+ *  - Query answers are bit-packed by START POSITION in `seq` (as Alg. 2
+ *    writes output[blockStartKmer + localIdx]): bit p of a uint32 array
+ *    (word p >> 5, bit p & 31) is 1 iff a valid k-mer starts at p and is
+ *    positive.  The array has ceil(seq_len / 32) words and is fully written.
+ *    read_hits[r] is the number of positive k-mers of read r.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    taking device pointers are asynchronous and stream-ordered like the
+ *    paper's device-facing entry points (Sec. IV-A); calls with a `_host`
+ *    suffix take host pointers and synchronise before returning.
+ *  - Every call returns SBF_OK or a negative status; on error nothing is
+ *    launched, outputs are untouched and sbf_last_error() (per thread) says
+ *    why.  Device faults are reported as SBF_ECUDA.
+ *  - Concurrent queries of one filter are safe.  An insert that overlaps a
+ *    query on the device makes the query see some subset of the inserted
+ *    bits (insertion is a monotone OR).
+ */
+#ifndef SBF_H
+#define SBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sbf_filter sbf_filter;
+typedef void* sbf_stream_t; /* cudaStream_t */
+
+enum {
+  SBF_OK = 0,
+  SBF_EINVAL = -1,        /* bad argument */
+  SBF_ENOMEM = -2,        /* device or host allocation failed */
+  SBF_ECUDA = -3,         /* a CUDA call failed */
+  SBF_EUNSUPPORTED = -4,  /* parameters outside the compiled set */
+  SBF_ETIMEOUT = -5,      /* a bounded device wait gave up */
+  SBF_EBUSY = -6          /* resource in use (server admission) */
+};
+
+/* ---------------------------------------------------------------------------
+ * Filter lifetime.
+ *
+ * sbf_create: 512-bit shards, canonical k-mers.  sbf_create_ex adds the shard
+ * size (256 or 512 bits) and `canonical` (1: every m-mer and s-mer is replaced
+ * by the smaller of its value and its reverse complement's, so a k-mer and
+ * its reverse complement are the same key; 0: forward strand only, the
+ * paper's literal behaviour).
+ *
+ * Parameters (Sec. IV-A, the paper's compile-time Config): 1 <= k <= 32,
+ * 1 <= m <= k, 1 <= s <= k, k - m + 1 <= 32, k - s <= 15, 1 <= H <= 16,
+ * bits >= shard_bits.  The number of shards is N = ceil(bits / shard_bits)
+ * (the paper rounds to a power of two; any N is valid here because the shard
+ * is chosen by a multiply-high, Sec. IV-B).  Returns SBF_EUNSUPPORTED for a
+ * parameter set without a compiled kernel.  The filter owns N * shard_bits / 8
+ * bytes of device memory on the current device, zeroed.
+ * ------------------------------------------------------------------------- */
+int sbf_create(int k, int m, int s, int H, uint64_t bits, sbf_filter** out);
+int sbf_create_ex(int k, int m, int s, int H, uint64_t bits, int shard_bits, int canonical,
+                  sbf_filter** out);
+/* Frees the device memory.  NULL is a no-op.  Must not be called while work
+ * on the filter is in flight. */
+void sbf_destroy(sbf_filter* f);
+
+/* Any output pointer may be NULL. */
+int sbf_info(const sbf_filter* f, int* k, int* m, int* s, int* H, int* shard_bits,
+             int* canonical, uint64_t* n_shards);
+/* Number of 64-bit words of the bit array (N * shard_bits / 64). */
+uint64_t sbf_num_words(const sbf_filter* f);
+/* Device address of the bit array (uint64 words, shard x = words
+ * [x*W, (x+1)*W), W = shard_bits / 64).  Owned by the filter. */
+const uint64_t* sbf_device_words(const sbf_filter* f);
+
+/* Zero all bits (stream-ordered). */
+int sbf_clear(sbf_filter* f, sbf_stream_t stream);
+
+/* Copy the bit array to / from host memory (sbf_num_words uint64 words);
+ * synchronous.  This is also the checkpoint format's payload. */
+int sbf_get_bits(const sbf_filter* f, uint64_t* h_words);
+int sbf_set_bits(sbf_filter* f, const uint64_t* h_words);
+
+/* ---------------------------------------------------------------------------
+ * Insert and query (Alg. 1 and Alg. 2).  Device pointers.
+ *
+ * sbf_insert_seqs: sets the bits of every valid k-mer of every read
+ *   (Alg. 1).  d_seq: seq_len bytes; d_off: n_reads + 1 uint64.
+ * sbf_query_seqs: d_kmer_bits: ceil(seq_len/32) uint32 (may be NULL);
+ *   d_read_hits: n_reads uint32 (may be NULL).  Both are overwritten.
+ * sbf_query_seqs_ex: as sbf_query_seqs, and if d_stats != NULL adds into
+ *   d_stats[0] the number of valid k-mers, d_stats[1] the number of
+ *   super-k-mer runs (maximal spans of consecutive valid k-mers of one read
+ *   with one minimizer: the shard loads the method needs, Sec. II-B) and
+ *   d_stats[2] the number of positive k-mers (three uint64 the caller zeroes).
+ * ------------------------------------------------------------------------- */
+int sbf_insert_seqs(sbf_filter* f, const uint8_t* d_seq, uint64_t seq_len,
+                    const uint64_t* d_off, uint64_t n_reads, sbf_stream_t stream);
+int sbf_query_seqs(const sbf_filter* f, const uint8_t* d_seq, uint64_t seq_len,
+                   const uint64_t* d_off, uint64_t n_reads, uint32_t* d_kmer_bits,
+                   uint32_t* d_read_hits, sbf_stream_t stream);
+int sbf_query_seqs_ex(const sbf_filter* f, const uint8_t* d_seq, uint64_t seq_len,
+                      const uint64_t* d_off, uint64_t n_reads, uint32_t* d_kmer_bits,
+                      uint32_t* d_read_hits, uint64_t* d_stats, sbf_stream_t stream);
+
+/* Host-resident input (Sec. V-F): the same operations on host buffers.  The
+ * input is copied to the device in chunks on two streams so that copies
+ * overlap the kernels; outputs are copied back.  Pinned host memory gives
+ * full link speed, pageable memory works.  Synchronous. */
+int sbf_insert_seqs_host(sbf_filter* f, const uint8_t* h_seq, uint64_t seq_len,
+                         const uint64_t* h_off, uint64_t n_reads);
+int sbf_query_seqs_host(const sbf_filter* f, const uint8_t* h_seq, uint64_t seq_len,
+                        const uint64_t* h_off, uint64_t n_reads, uint32_t* h_kmer_bits,
+                        uint32_t* h_read_hits);
+
+/* Number of k-mer start positions sum_r max(0, len_r - k + 1) of a host
+ * offset table (valid or not). */
+int sbf_num_kmers(const uint64_t* h_off, uint64_t n_reads, int k, uint64_t* out);
+
+/* Human-readable reason of the calling thread's last failure ("" if none). */
+const char* sbf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBF_H */

@@ -1,0 +1,447 @@
+// sbf_api.cu -- the C ABI of libsbf (declared in include/sbf.h): parameter
+// validation, filter lifetime, dispatch to the fused or generic kernels, and
+// the host-input path (chunked copies overlapped with kernels on two streams,
+// the paper's host-facing entry points, Sec. IV-A and Sec. V-F).
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sbf_internal.h"
+
+namespace sbf {
+
+static thread_local char g_err[512] = {0};
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SBF_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+void clear_error() { g_err[0] = 0; }
+
+int sm_count() {
+  static thread_local int dev_cached = -1;
+  static thread_local int count = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != dev_cached) {
+    cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
+    if (count <= 0) count = 1;
+    dev_cached = dev;
+  }
+  return count;
+}
+
+}  // namespace sbf
+
+using namespace sbf;
+
+namespace {
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int check_params(int k, int m, int s, int H, uint64_t bits, int shard_bits) {
+  if (k < 1 || k > 32) return fail(SBF_EINVAL, "k=%d outside [1, 32]", k);
+  if (m < 1 || m > k) return fail(SBF_EINVAL, "m=%d outside [1, k=%d]", m, k);
+  if (s < 1 || s > k) return fail(SBF_EINVAL, "s=%d outside [1, k=%d]", s, k);
+  if (k - m + 1 > 32) return fail(SBF_EINVAL, "window k-m+1=%d exceeds 32", k - m + 1);
+  if (k - s > 15) return fail(SBF_EINVAL, "k-s=%d exceeds 15", k - s);
+  if (H < 1 || H > 16) return fail(SBF_EINVAL, "H=%d outside [1, 16]", H);
+  if (shard_bits != 256 && shard_bits != 512)
+    return fail(SBF_EINVAL, "shard_bits=%d not 256 or 512", shard_bits);
+  if (bits < (uint64_t)shard_bits)
+    return fail(SBF_EINVAL, "bits=%llu below one shard", (unsigned long long)bits);
+  if (bits > (1ull << 46)) return fail(SBF_EINVAL, "bits=%llu above 2^46", (unsigned long long)bits);
+  return SBF_OK;
+}
+
+int launch_insert(sbf_filter* f, const uint8_t* seq, uint64_t seq_len, const uint64_t* off,
+                  uint64_t n_reads, cudaStream_t st) {
+  cudaError_t e = f->fused ? fused_insert(f->geom, seq, seq_len, off, n_reads, st)
+                           : generic_insert(f->geom, seq, seq_len, off, n_reads, st);
+  return e == cudaSuccess ? SBF_OK : cuda_fail(e, "insert launch");
+}
+
+int launch_query(const sbf_filter* f, const uint8_t* seq, uint64_t seq_len, const uint64_t* off,
+                 uint64_t n_reads, uint32_t* bits, uint32_t* hits, uint64_t* stats,
+                 cudaStream_t st) {
+  cudaError_t e = f->fused ? fused_query(f->geom, seq, seq_len, off, n_reads, bits, hits, stats, st)
+                           : generic_query(f->geom, seq, seq_len, off, n_reads, bits, hits, stats, st);
+  return e == cudaSuccess ? SBF_OK : cuda_fail(e, "query launch");
+}
+
+int check_seq_args(const void* seq, uint64_t seq_len, const void* off, uint64_t n_reads) {
+  if (n_reads > 0 && !off) return fail(SBF_EINVAL, "offsets pointer is NULL");
+  if (seq_len > 0 && !seq) return fail(SBF_EINVAL, "sequence pointer is NULL");
+  if (seq_len >= (1ull << 62)) return fail(SBF_EINVAL, "seq_len too large");
+  return SBF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sbf_last_error(void) { return g_err; }
+
+int sbf_create_ex(int k, int m, int s, int H, uint64_t bits, int shard_bits, int canonical,
+                  sbf_filter** out) {
+  clear_error();
+  if (!out) return fail(SBF_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = check_params(k, m, s, H, bits, shard_bits);
+  if (rc != SBF_OK) return rc;
+  uint64_t n_shards = (bits + (uint64_t)shard_bits - 1) / (uint64_t)shard_bits;
+  uint64_t n_words = n_shards * (uint64_t)(shard_bits / 64);
+  sbf_filter* f = new (std::nothrow) sbf_filter();
+  if (!f) return fail(SBF_ENOMEM, "host allocation failed");
+  cudaError_t e = cudaGetDevice(&f->device);
+  if (e != cudaSuccess) {
+    delete f;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  uint64_t* words = nullptr;
+  e = cudaMalloc(&words, n_words * sizeof(uint64_t));
+  if (e != cudaSuccess) {
+    delete f;
+    cudaGetLastError();
+    return fail(SBF_ENOMEM, "cudaMalloc of %llu bytes failed: %s",
+                (unsigned long long)(n_words * 8), cudaGetErrorString(e));
+  }
+  e = cudaMemset(words, 0, n_words * sizeof(uint64_t));
+  if (e != cudaSuccess) {
+    cudaFree(words);
+    delete f;
+    return cuda_fail(e, "cudaMemset");
+  }
+  f->geom = make_geom(words, n_shards, k, m, s, H, shard_bits, canonical ? 1 : 0);
+  f->n_words = n_words;
+  f->fused = fused_supported(f->geom);
+  *out = f;
+  return SBF_OK;
+}
+
+int sbf_create(int k, int m, int s, int H, uint64_t bits, sbf_filter** out) {
+  return sbf_create_ex(k, m, s, H, bits, 512, 1, out);
+}
+
+void sbf_destroy(sbf_filter* f) {
+  if (!f) return;
+  DeviceGuard dg(f->device);
+  for (int i = 0; i < 2; ++i) {
+    if (f->host_streams[i]) cudaStreamDestroy(f->host_streams[i]);
+    cudaFree(f->host_dev_seq[i]);
+    cudaFree(f->host_dev_off[i]);
+    cudaFree(f->host_dev_bits[i]);
+    cudaFree(f->host_dev_hits[i]);
+  }
+  cudaFree(f->geom.words);
+  delete f;
+}
+
+int sbf_info(const sbf_filter* f, int* k, int* m, int* s, int* H, int* shard_bits, int* canonical,
+             uint64_t* n_shards) {
+  clear_error();
+  if (!f) return fail(SBF_EINVAL, "filter is NULL");
+  if (k) *k = f->geom.k;
+  if (m) *m = f->geom.m;
+  if (s) *s = f->geom.s;
+  if (H) *H = f->geom.H;
+  if (shard_bits) *shard_bits = f->geom.shard_bits;
+  if (canonical) *canonical = f->geom.canonical;
+  if (n_shards) *n_shards = f->geom.n_shards;
+  return SBF_OK;
+}
+
+uint64_t sbf_num_words(const sbf_filter* f) { return f ? f->n_words : 0; }
+
+const uint64_t* sbf_device_words(const sbf_filter* f) { return f ? f->geom.words : nullptr; }
+
+int sbf_clear(sbf_filter* f, sbf_stream_t stream) {
+  clear_error();
+  if (!f) return fail(SBF_EINVAL, "filter is NULL");
+  DeviceGuard dg(f->device);
+  cudaError_t e = cudaMemsetAsync(f->geom.words, 0, f->n_words * 8, (cudaStream_t)stream);
+  return e == cudaSuccess ? SBF_OK : cuda_fail(e, "clear");
+}
+
+int sbf_get_bits(const sbf_filter* f, uint64_t* h_words) {
+  clear_error();
+  if (!f || !h_words) return fail(SBF_EINVAL, "NULL argument");
+  DeviceGuard dg(f->device);
+  cudaError_t e = cudaMemcpy(h_words, f->geom.words, f->n_words * 8, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? SBF_OK : cuda_fail(e, "get_bits");
+}
+
+int sbf_set_bits(sbf_filter* f, const uint64_t* h_words) {
+  clear_error();
+  if (!f || !h_words) return fail(SBF_EINVAL, "NULL argument");
+  DeviceGuard dg(f->device);
+  cudaError_t e = cudaMemcpy(f->geom.words, h_words, f->n_words * 8, cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? SBF_OK : cuda_fail(e, "set_bits");
+}
+
+int sbf_insert_seqs(sbf_filter* f, const uint8_t* d_seq, uint64_t seq_len, const uint64_t* d_off,
+                    uint64_t n_reads, sbf_stream_t stream) {
+  clear_error();
+  if (!f) return fail(SBF_EINVAL, "filter is NULL");
+  int rc = check_seq_args(d_seq, seq_len, d_off, n_reads);
+  if (rc != SBF_OK) return rc;
+  DeviceGuard dg(f->device);
+  return launch_insert(f, d_seq, seq_len, d_off, n_reads, (cudaStream_t)stream);
+}
+
+int sbf_query_seqs_ex(const sbf_filter* f, const uint8_t* d_seq, uint64_t seq_len,
+                      const uint64_t* d_off, uint64_t n_reads, uint32_t* d_kmer_bits,
+                      uint32_t* d_read_hits, uint64_t* d_stats, sbf_stream_t stream) {
+  clear_error();
+  if (!f) return fail(SBF_EINVAL, "filter is NULL");
+  int rc = check_seq_args(d_seq, seq_len, d_off, n_reads);
+  if (rc != SBF_OK) return rc;
+  DeviceGuard dg(f->device);
+  return launch_query(f, d_seq, seq_len, d_off, n_reads, d_kmer_bits, d_read_hits, d_stats,
+                      (cudaStream_t)stream);
+}
+
+int sbf_query_seqs(const sbf_filter* f, const uint8_t* d_seq, uint64_t seq_len,
+                   const uint64_t* d_off, uint64_t n_reads, uint32_t* d_kmer_bits,
+                   uint32_t* d_read_hits, sbf_stream_t stream) {
+  return sbf_query_seqs_ex(f, d_seq, seq_len, d_off, n_reads, d_kmer_bits, d_read_hits, nullptr,
+                           stream);
+}
+
+int sbf_num_kmers(const uint64_t* h_off, uint64_t n_reads, int k, uint64_t* out) {
+  clear_error();
+  if (!out || (n_reads && !h_off) || k < 1) return fail(SBF_EINVAL, "bad argument");
+  uint64_t total = 0;
+  for (uint64_t r = 0; r < n_reads; ++r) {
+    uint64_t len = h_off[r + 1] > h_off[r] ? h_off[r + 1] - h_off[r] : 0;
+    if (len >= (uint64_t)k) total += len - (uint64_t)k + 1;
+  }
+  *out = total;
+  return SBF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Host-input path.  The reads are cut into chunks at read boundaries (about
+// kChunkBytes each; a read longer than that is a chunk of its own).  Chunk c
+// uses buffer set c & 1 and stream c & 1, so the copy of one chunk overlaps
+// the kernel of the other.
+//
+// Insert chunks start exactly at their first read.  Query chunks start at the
+// 32-aligned position A <= off[r0] so that their output words line up with
+// the caller's; the bytes [A, off[r0]) (which may hold pieces of several
+// earlier reads) form a leading dummy read whose answers are masked out and
+// whose hit count is dropped.  The first output word of a query chunk is
+// shared with the previous chunk and is merged on the host after both finish.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint64_t kDefaultChunkBytes = 256ull << 20;
+
+// SBF_HOST_CHUNK_BYTES overrides the chunk size (tests use small chunks to
+// exercise the chunk seams).
+uint64_t chunk_bytes() {
+  const char* env = getenv("SBF_HOST_CHUNK_BYTES");
+  if (env && *env) {
+    unsigned long long v = strtoull(env, nullptr, 10);
+    if (v >= 64) return v;
+  }
+  return kDefaultChunkBytes;
+}
+
+struct Chunk {
+  uint64_t r0, r1;   // reads [r0, r1)
+  uint64_t a;        // device position 0 of the chunk
+  uint64_t end;      // off[r1]
+};
+
+std::vector<Chunk> plan_chunks(const uint64_t* off, uint64_t n_reads, bool align32) {
+  std::vector<Chunk> out;
+  const uint64_t kChunkBytes = chunk_bytes();
+  uint64_t r = 0;
+  while (r < n_reads) {
+    uint64_t a = align32 ? (off[r] & ~31ull) : off[r];
+    uint64_t r1 = r + 1;
+    while (r1 < n_reads && off[r1 + 1] - a <= kChunkBytes) ++r1;
+    out.push_back(Chunk{r, r1, a, off[r1]});
+    r = r1;
+  }
+  return out;
+}
+
+int ensure_host_buffers(sbf_filter* f, uint64_t seq_cap, uint64_t reads_cap) {
+  for (int i = 0; i < 2; ++i) {
+    if (!f->host_streams[i]) {
+      cudaError_t e = cudaStreamCreateWithFlags(&f->host_streams[i], cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "stream create");
+    }
+  }
+  if (seq_cap > f->host_cap_seq) {
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(f->host_dev_seq[i]);
+      cudaFree(f->host_dev_bits[i]);
+      f->host_dev_seq[i] = nullptr;
+      f->host_dev_bits[i] = nullptr;
+      if (cudaMalloc(&f->host_dev_seq[i], seq_cap) != cudaSuccess ||
+          cudaMalloc(&f->host_dev_bits[i], ((seq_cap + 31) / 32) * 4) != cudaSuccess) {
+        cudaGetLastError();
+        f->host_cap_seq = 0;
+        return fail(SBF_ENOMEM, "device staging allocation failed");
+      }
+    }
+    f->host_cap_seq = seq_cap;
+  }
+  if (reads_cap > f->host_cap_reads) {
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(f->host_dev_off[i]);
+      cudaFree(f->host_dev_hits[i]);
+      f->host_dev_off[i] = nullptr;
+      f->host_dev_hits[i] = nullptr;
+      if (cudaMalloc(&f->host_dev_off[i], (reads_cap + 1) * 8) != cudaSuccess ||
+          cudaMalloc(&f->host_dev_hits[i], reads_cap * 4) != cudaSuccess) {
+        cudaGetLastError();
+        f->host_cap_reads = 0;
+        return fail(SBF_ENOMEM, "device staging allocation failed");
+      }
+    }
+    f->host_cap_reads = reads_cap;
+  }
+  return SBF_OK;
+}
+
+int host_run(sbf_filter* f, bool is_query, const uint8_t* h_seq, uint64_t seq_len,
+             const uint64_t* h_off, uint64_t n_reads, uint32_t* h_bits, uint32_t* h_hits) {
+  if (n_reads == 0) {
+    if (h_bits && seq_len) memset(h_bits, 0, ((seq_len + 31) / 32) * 4);
+    return SBF_OK;
+  }
+  for (uint64_t r = 0; r < n_reads; ++r)
+    if (h_off[r + 1] < h_off[r])
+      return fail(SBF_EINVAL, "offsets decrease at read %llu", (unsigned long long)r);
+  if (h_off[0] != 0 || h_off[n_reads] != seq_len)
+    return fail(SBF_EINVAL, "offsets must start at 0 and end at seq_len");
+  const uint64_t dummy = is_query ? 1 : 0;  // leading dummy read of query chunks
+  std::vector<Chunk> chunks = plan_chunks(h_off, n_reads, is_query);
+  uint64_t seq_cap = 0, reads_cap = 0;
+  for (const Chunk& c : chunks) {
+    seq_cap = std::max(seq_cap, c.end - c.a);
+    reads_cap = std::max(reads_cap, c.r1 - c.r0 + dummy);
+  }
+  std::lock_guard<std::mutex> lock(f->host_mu);
+  DeviceGuard dg(f->device);
+  int rc = ensure_host_buffers(f, seq_cap, reads_cap);
+  if (rc != SBF_OK) return rc;
+  std::vector<uint64_t> offs[2];
+  std::vector<uint32_t> first_words(chunks.size(), 0);
+  for (size_t ci = 0; ci < chunks.size(); ++ci) {
+    const Chunk& c = chunks[ci];
+    int b = (int)(ci & 1);
+    cudaStream_t st = f->host_streams[b];
+    // buffer set b (and offs[b]) is free once its previous chunk is done
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "host path sync");
+    std::vector<uint64_t>& o = offs[b];
+    uint64_t nr = c.r1 - c.r0 + dummy;
+    o.resize(nr + 1);
+    o[0] = 0;
+    for (uint64_t r = c.r0; r <= c.r1; ++r) o[r - c.r0 + dummy] = h_off[r] - c.a;
+    uint64_t len = c.end - c.a;
+    if ((e = cudaMemcpyAsync(f->host_dev_seq[b], h_seq + c.a, len, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(f->host_dev_off[b], o.data(), (nr + 1) * 8, cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess)
+      return cuda_fail(e, "host path H2D");
+    if (!is_query) {
+      rc = launch_insert(f, f->host_dev_seq[b], len, f->host_dev_off[b], nr, st);
+      if (rc != SBF_OK) return rc;
+      continue;
+    }
+    rc = launch_query(f, f->host_dev_seq[b], len, f->host_dev_off[b], nr,
+                      h_bits ? f->host_dev_bits[b] : nullptr,
+                      h_hits ? f->host_dev_hits[b] : nullptr, nullptr, st);
+    if (rc != SBF_OK) return rc;
+    uint64_t nwords = (len + 31) / 32;
+    if (h_bits) {
+      uint64_t w0 = c.a / 32;
+      if (nwords > 1 &&
+          (e = cudaMemcpyAsync(h_bits + w0 + 1, f->host_dev_bits[b] + 1, (nwords - 1) * 4,
+                               cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "host path D2H");
+      if ((e = cudaMemcpyAsync(&first_words[ci], f->host_dev_bits[b], 4, cudaMemcpyDeviceToHost,
+                               st)) != cudaSuccess)
+        return cuda_fail(e, "host path D2H");
+    }
+    if (h_hits && (e = cudaMemcpyAsync(h_hits + c.r0, f->host_dev_hits[b] + 1, (nr - 1) * 4,
+                                       cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(e, "host path D2H");
+  }
+  for (int b = 0; b < 2; ++b) {
+    cudaError_t e = cudaStreamSynchronize(f->host_streams[b]);
+    if (e != cudaSuccess) return cuda_fail(e, "host path sync");
+  }
+  if (is_query && h_bits) {
+    // Every output word is written: words [A/32 + 1, ceil(end/32)) by the
+    // chunk's copy, word A/32 here.  Its bits below off[r0] belong to the
+    // previous chunk, which wrote them (and zeros above) when it ended there.
+    for (size_t ci = 0; ci < chunks.size(); ++ci) {
+      const Chunk& c = chunks[ci];
+      uint64_t lead = h_off[c.r0] - c.a;
+      uint32_t mine = first_words[ci] & (lead >= 32 ? 0u : (~0u << lead));
+      uint64_t w0 = c.a / 32;
+      uint32_t prev = (ci > 0 && chunks[ci - 1].end > c.a) ? h_bits[w0] : 0u;
+      h_bits[w0] = prev | mine;
+    }
+  }
+  return SBF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbf_insert_seqs_host(sbf_filter* f, const uint8_t* h_seq, uint64_t seq_len,
+                         const uint64_t* h_off, uint64_t n_reads) {
+  clear_error();
+  if (!f) return fail(SBF_EINVAL, "filter is NULL");
+  int rc = check_seq_args(h_seq, seq_len, h_off, n_reads);
+  if (rc != SBF_OK) return rc;
+  return host_run(f, false, h_seq, seq_len, h_off, n_reads, nullptr, nullptr);
+}
+
+int sbf_query_seqs_host(const sbf_filter* f, const uint8_t* h_seq, uint64_t seq_len,
+                        const uint64_t* h_off, uint64_t n_reads, uint32_t* h_kmer_bits,
+                        uint32_t* h_read_hits) {
+  clear_error();
+  if (!f) return fail(SBF_EINVAL, "filter is NULL");
+  int rc = check_seq_args(h_seq, seq_len, h_off, n_reads);
+  if (rc != SBF_OK) return rc;
+  // the host staging state is mutable; queries stay logically const
+  return host_run(const_cast<sbf_filter*>(f), true, h_seq, seq_len, h_off, n_reads, h_kmer_bits,
+                  h_read_hits);
+}
+
+}  // extern "C"

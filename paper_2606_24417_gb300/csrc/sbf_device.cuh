@@ -1,0 +1,106 @@
+// sbf_device.cuh -- device-side definition of the Super Bloom filter's hashes
+// and layout, shared by all kernels of the library.
+//
+// cuSBF paper references: 2-bit packing with the first base most significant
+// (Sec. IV-C), minimizer by one multiplicative mix and s-mer hash by a
+// stronger xorshift-multiply mix (Sec. IV-G "role-specialised hashing"),
+// sectorised shards with hash i in sector i mod S (Sec. IV-B), bit-slicing
+// and the salted-multiply fallback (Sec. IV-G), Findere AND (Eq. 2, Alg. 2).
+//
+// Constants: Knuth's golden-ratio multiplier floor(2^64/phi) (and its top 32
+// bits), the SplitMix64 finaliser (Steele, Lea & Flood 2014), and Knuth's
+// MMIX LCG multiplier / increment as the s-mer and shard keys.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace sbf {
+
+constexpr uint64_t kGolden64 = 0x9E3779B97F4A7C15ull;
+constexpr uint32_t kGolden32 = 0x9E3779B9u;
+constexpr uint64_t kMixMul1 = 0xBF58476D1CE4E5B9ull;
+constexpr uint64_t kMixMul2 = 0x94D049BB133111EBull;
+constexpr uint64_t kSmerKey = 0x5851F42D4C957F2Dull;   // 6364136223846793005
+constexpr uint64_t kShardKey = 0x14057B7EF767814Full;  // 1442695040888963407
+
+// Runtime description of one filter, passed by value to kernels.
+struct Geom {
+  uint64_t* words;     // N * W uint64 words
+  uint64_t n_shards;   // N
+  int k, m, s, H;
+  int shard_bits;      // B
+  int canonical;
+  int sectors;         // S = min(H, B/64)
+  int sector_bits;     // B / S
+  int sector_log2;     // b = log2(B / S)
+  int slice;           // q = floor(64 / H)
+};
+
+__host__ __device__ inline Geom make_geom(uint64_t* words, uint64_t n_shards, int k, int m, int s,
+                                          int H, int shard_bits, int canonical) {
+  Geom g;
+  g.words = words;
+  g.n_shards = n_shards;
+  g.k = k; g.m = m; g.s = s; g.H = H;
+  g.shard_bits = shard_bits;
+  g.canonical = canonical;
+  int W = shard_bits / 64;
+  g.sectors = H < W ? H : W;
+  g.sector_bits = shard_bits / g.sectors;
+  int b = 0;
+  while ((1 << b) < g.sector_bits) ++b;
+  g.sector_log2 = b;
+  g.slice = 64 / H;
+  return g;
+}
+
+// SplitMix64 finaliser.
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  x ^= x >> 30;
+  x *= kMixMul1;
+  x ^= x >> 27;
+  x *= kMixMul2;
+  x ^= x >> 31;
+  return x;
+}
+
+// 2-bit code of an ASCII base: ((c >> 1) ^ (c >> 2)) & 3 maps A/a->0, C/c->1,
+// G/g->2, T/t->3.  Validity is checked separately.
+__device__ __forceinline__ uint32_t base_code(uint32_t ch) { return ((ch >> 1) ^ (ch >> 2)) & 3u; }
+
+__device__ __forceinline__ bool base_valid(uint32_t ch) {
+  uint32_t lc = ch | 0x20u;
+  return lc == 'a' || lc == 'c' || lc == 'g' || lc == 't';
+}
+
+// Minimizer order key of a canonical m-mer: bijective multiplicative hash in
+// the narrowest machine word holding 2m bits.
+__device__ __forceinline__ uint64_t order_key(uint64_t v, int m) {
+  return (2 * m <= 32) ? (uint64_t)((uint32_t)v * kGolden32) : v * kGolden64;
+}
+
+__device__ __forceinline__ uint64_t shard_of(uint64_t mu, uint64_t n_shards) {
+  return __umul64hi(mix64(mu ^ kShardKey), n_shards);
+}
+
+__device__ __forceinline__ uint64_t smer_hash(uint64_t v) { return mix64(v ^ kSmerKey); }
+
+// Bit index inside a shard for hash function i (runtime geometry).
+__device__ __forceinline__ uint32_t bit_in_shard(const Geom& g, uint64_t h, int i) {
+  uint32_t p;
+  if (g.slice >= g.sector_log2) {
+    p = (uint32_t)(h >> (i * g.slice)) & (uint32_t)(g.sector_bits - 1);
+  } else {
+    uint64_t salt = kGolden64 * (uint64_t)(2 * i + 1);
+    p = (uint32_t)((h * salt) >> (64 - g.sector_log2));
+  }
+  return (uint32_t)(i % g.sectors) * (uint32_t)g.sector_bits + p;
+}
+
+__device__ __forceinline__ uint64_t len_mask(int len) {
+  return len >= 32 ? ~0ull : ((1ull << (2 * len)) - 1ull);
+}
+
+}  // namespace sbf

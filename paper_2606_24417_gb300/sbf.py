@@ -1,0 +1,240 @@
+"""ctypes binding of libsbf (include/sbf.h).  Argument marshalling only.
+
+Device inputs are torch CUDA tensors (uint8 sequences, int64 offsets, which
+the library reads as uint64); host inputs are numpy arrays.  Every operation
+runs in libsbf's kernels; if the library is not built the first call raises
+``SbfError`` -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+import threading
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libsbf.so")
+_lib = None
+_lock = threading.Lock()
+
+SBF_OK = 0
+_STATUS = {
+    -1: "SBF_EINVAL", -2: "SBF_ENOMEM", -3: "SBF_ECUDA", -4: "SBF_EUNSUPPORTED",
+    -5: "SBF_ETIMEOUT", -6: "SBF_EBUSY",
+}
+
+
+class SbfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library() -> ctypes.CDLL:
+    """Load libsbf.so (in-tree build).  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise SbfError(-4, f"{_LIB_PATH} is not built; run __graft_entry__.build()")
+        lib = ctypes.CDLL(_LIB_PATH)
+        P, U64, I, U32P = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
+        sig = {
+            "sbf_create": (I, [I, I, I, I, U64, ctypes.POINTER(P)]),
+            "sbf_create_ex": (I, [I, I, I, I, U64, I, I, ctypes.POINTER(P)]),
+            "sbf_destroy": (None, [P]),
+            "sbf_info": (I, [P] + [ctypes.POINTER(I)] * 6 + [ctypes.POINTER(U64)]),
+            "sbf_num_words": (U64, [P]),
+            "sbf_device_words": (P, [P]),
+            "sbf_clear": (I, [P, P]),
+            "sbf_get_bits": (I, [P, P]),
+            "sbf_set_bits": (I, [P, P]),
+            "sbf_insert_seqs": (I, [P, P, U64, P, U64, P]),
+            "sbf_query_seqs": (I, [P, P, U64, P, U64, U32P, U32P, P]),
+            "sbf_query_seqs_ex": (I, [P, P, U64, P, U64, U32P, U32P, P, P]),
+            "sbf_insert_seqs_host": (I, [P, P, U64, P, U64]),
+            "sbf_query_seqs_host": (I, [P, P, U64, P, U64, U32P, U32P]),
+            "sbf_num_kmers": (I, [P, U64, I, ctypes.POINTER(U64)]),
+            "sbf_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc: int) -> None:
+    if rc != SBF_OK:
+        msg = load_library().sbf_last_error()
+        raise SbfError(rc, msg.decode() if msg else "")
+
+
+def _stream_handle(stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype_size: int | None = None) -> int:
+    if t is None:
+        return 0
+    if not t.is_cuda:
+        raise SbfError(-1, "expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise SbfError(-1, "expected a contiguous tensor")
+    if dtype_size is not None and t.element_size() != dtype_size:
+        raise SbfError(-1, f"expected {dtype_size}-byte elements, got {t.dtype}")
+    return int(t.data_ptr())
+
+
+def _host_ptr(a) -> int:
+    return int(a.ctypes.data) if a is not None and a.size else 0
+
+
+class SuperBloomFilter:
+    """A Super Bloom filter resident in device memory (owned by libsbf).
+
+    k, m, s, H: k-mer, minimizer and Findere s-mer lengths and hash count;
+    bits: filter size (rounded up to whole shards); shard_bits: 256 or 512;
+    canonical: treat a k-mer and its reverse complement as one key.
+    """
+
+    def __init__(self, k: int = 31, m: int = 16, s: int = 28, H: int = 4, bits: int = 1 << 30,
+                 shard_bits: int = 512, canonical: bool = True):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.sbf_create_ex(k, m, s, H, bits, shard_bits, 1 if canonical else 0,
+                                 ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+        ki, mi, si, Hi, Bi, ci = (ctypes.c_int() for _ in range(6))
+        n = ctypes.c_uint64()
+        _check(lib.sbf_info(h, ctypes.byref(ki), ctypes.byref(mi), ctypes.byref(si),
+                            ctypes.byref(Hi), ctypes.byref(Bi), ctypes.byref(ci), ctypes.byref(n)))
+        self.k, self.m, self.s, self.H = ki.value, mi.value, si.value, Hi.value
+        self.shard_bits, self.canonical = Bi.value, bool(ci.value)
+        self.n_shards = int(n.value)
+        self.n_words = int(lib.sbf_num_words(h))
+
+    def close(self) -> None:
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.sbf_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    @property
+    def nbytes(self) -> int:
+        return self.n_words * 8
+
+    def device_words_ptr(self) -> int:
+        return int(self._lib.sbf_device_words(self._h))
+
+    # -- device-resident batches ------------------------------------------
+    def insert(self, seq, off, stream=None) -> None:
+        """seq: uint8 CUDA tensor; off: int64 CUDA tensor of n_reads + 1 offsets."""
+        _check(self._lib.sbf_insert_seqs(self._h, _dev_ptr(seq, 1), seq.numel(), _dev_ptr(off, 8),
+                                         off.numel() - 1, _stream_handle(stream)))
+
+    def query(self, seq, off, bits=None, hits=None, stats=None, stream=None, want_bits=True,
+              want_hits=True):
+        """Returns (bits int32[ceil(len/32)], hits int32[n_reads]) CUDA tensors.
+
+        The int32 tensors hold the library's uint32 words (reinterpret with
+        ``.view(torch.uint32)`` or mask with 0xFFFFFFFF)."""
+        import torch
+
+        n = off.numel() - 1
+        if bits is None and want_bits:
+            bits = torch.empty((seq.numel() + 31) // 32, dtype=torch.int32, device=seq.device)
+        if hits is None and want_hits:
+            hits = torch.empty(max(n, 0), dtype=torch.int32, device=seq.device)
+        _check(self._lib.sbf_query_seqs_ex(self._h, _dev_ptr(seq, 1), seq.numel(), _dev_ptr(off, 8),
+                                           n, _dev_ptr(bits, 4), _dev_ptr(hits, 4),
+                                           _dev_ptr(stats, 8), _stream_handle(stream)))
+        return bits, hits
+
+    def clear(self, stream=None) -> None:
+        _check(self._lib.sbf_clear(self._h, _stream_handle(stream)))
+
+    # -- host-resident batches --------------------------------------------
+    def insert_host(self, seq: np.ndarray, off: np.ndarray) -> None:
+        seq = np.ascontiguousarray(seq, dtype=np.uint8)
+        off = np.ascontiguousarray(off, dtype=np.uint64)
+        _check(self._lib.sbf_insert_seqs_host(self._h, _host_ptr(seq), seq.size, _host_ptr(off),
+                                              off.size - 1))
+
+    def query_host(self, seq: np.ndarray, off: np.ndarray, bits: np.ndarray | None = None,
+                   hits: np.ndarray | None = None):
+        seq = np.ascontiguousarray(seq, dtype=np.uint8)
+        off = np.ascontiguousarray(off, dtype=np.uint64)
+        if bits is None:
+            bits = np.empty((seq.size + 31) // 32, dtype=np.uint32)
+        if hits is None:
+            hits = np.empty(off.size - 1, dtype=np.uint32)
+        _check(self._lib.sbf_query_seqs_host(self._h, _host_ptr(seq), seq.size, _host_ptr(off),
+                                             off.size - 1, _host_ptr(bits), _host_ptr(hits)))
+        return bits, hits
+
+    # -- bit array and checkpoints -----------------------------------------
+    def words(self) -> np.ndarray:
+        out = np.empty(self.n_words, dtype=np.uint64)
+        _check(self._lib.sbf_get_bits(self._h, _host_ptr(out)))
+        return out
+
+    def set_words(self, w: np.ndarray) -> None:
+        w = np.ascontiguousarray(w, dtype=np.uint64)
+        if w.size != self.n_words:
+            raise SbfError(-1, f"expected {self.n_words} words, got {w.size}")
+        _check(self._lib.sbf_set_bits(self._h, _host_ptr(w)))
+
+    _MAGIC = b"SBFGB300"
+    _VERSION = 1
+
+    def save(self, path: str) -> None:
+        """Checkpoint: header (magic, version, k, m, s, H, shard_bits,
+        canonical, n_shards) followed by the raw little-endian words."""
+        hdr = struct.pack("<8sIiiiiiiQ", self._MAGIC, self._VERSION, self.k, self.m, self.s,
+                          self.H, self.shard_bits, int(self.canonical), self.n_shards)
+        with open(path, "wb") as fh:
+            fh.write(hdr)
+            fh.write(self.words().astype("<u8").tobytes())
+
+    @classmethod
+    def load(cls, path: str) -> "SuperBloomFilter":
+        size = struct.calcsize("<8sIiiiiiiQ")
+        with open(path, "rb") as fh:
+            hdr = fh.read(size)
+            magic, ver, k, m, s, H, B, canon, n = struct.unpack("<8sIiiiiiiQ", hdr)
+            if magic != cls._MAGIC or ver != cls._VERSION:
+                raise SbfError(-1, f"{path}: not a filter checkpoint")
+            f = cls(k, m, s, H, n * B, shard_bits=B, canonical=bool(canon))
+            w = np.frombuffer(fh.read(), dtype="<u8")
+            f.set_words(w)
+        return f
+
+
+def num_kmers(off: np.ndarray, k: int) -> int:
+    off = np.ascontiguousarray(off, dtype=np.uint64)
+    out = ctypes.c_uint64()
+    _check(load_library().sbf_num_kmers(_host_ptr(off), off.size - 1, k, ctypes.byref(out)))
+    return int(out.value)

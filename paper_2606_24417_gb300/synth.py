@@ -14,8 +14,23 @@ reads, lognormal read lengths and Poisson request arrivals.
 from __future__ import annotations
 
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
+
+
+def _parallel(fn, items):
+    """Run fn over items on threads (numpy releases the GIL in its loops);
+    threads, not processes, so it is safe after CUDA initialisation."""
+    items = list(items)
+    workers = min(len(items), os.cpu_count() or 1, 32)
+    if workers <= 1:
+        for it in items:
+            fn(it)
+        return
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        list(ex.map(fn, items))
 
 _ACGT = np.frombuffer(b"ACGT", dtype=np.uint8)
 _COMPLEMENT = np.arange(256, dtype=np.uint8)
@@ -44,10 +59,14 @@ def _stream_key(seed: int, stream: int) -> np.uint64:
 
 def u64(seed: int, stream: int, start: int, n: int) -> np.ndarray:
     """n counter-based 64-bit random words: element i depends only on (seed, stream, start+i)."""
+    return u64_at(seed, stream, np.arange(start, start + n, dtype=np.uint64))
+
+
+def u64_at(seed: int, stream: int, idx: np.ndarray) -> np.ndarray:
+    """Counter-based 64-bit random words at arbitrary counters idx."""
     key = _stream_key(seed, stream)
-    idx = np.arange(start, start + n, dtype=np.uint64)
     with np.errstate(over="ignore"):
-        return _fmix64(idx * np.uint64(0xD6E8FEB86659FD93) + key)
+        return _fmix64(np.asarray(idx, dtype=np.uint64) * np.uint64(0xD6E8FEB86659FD93) + key)
 
 
 def uniform01(seed: int, stream: int, start: int, n: int) -> np.ndarray:
@@ -55,26 +74,31 @@ def uniform01(seed: int, stream: int, start: int, n: int) -> np.ndarray:
     return (u64(seed, stream, start, n) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
 
 
-def randint(seed: int, stream: int, n: int, lo: int, hi: int) -> np.ndarray:
-    """Integers uniform in [lo, hi) (multiply-shift on 53-bit uniforms)."""
+def randint(seed: int, stream: int, n: int, lo: int, hi: int, start: int = 0) -> np.ndarray:
+    """Integers uniform in [lo, hi) (multiply-shift on 53-bit uniforms);
+    element i uses counter start + i."""
     span = hi - lo
-    return lo + np.floor(uniform01(seed, stream, 0, n) * span).astype(np.int64)
+    return lo + np.floor(uniform01(seed, stream, start, n) * span).astype(np.int64)
 
 
 # ----------------------------------------------------------------------------
 # sequences
 # ----------------------------------------------------------------------------
+_BYTE_TO_BASES = _ACGT[(np.arange(256)[:, None] >> (2 * np.arange(4))[None, :]) & 3].astype(np.uint8)
+
+
 def uniform_dna(n: int, seed: int) -> np.ndarray:
-    """n uniform random bases (uint8 ASCII 'ACGT')."""
+    """n uniform random bases (uint8 ASCII 'ACGT'): each random byte gives four
+    bases (2 bits each, low bits first)."""
     out = np.empty(n, dtype=np.uint8)
     chunk = 1 << 24
-    for s in range(0, n, chunk):
+
+    def fill(s):
         e = min(n, s + chunk)
         w = u64(seed, 1, s // 32, (e - s + 31) // 32)
-        two = np.empty((w.size, 32), dtype=np.uint8)
-        for j in range(32):
-            two[:, j] = ((w >> np.uint64(2 * j)) & np.uint64(3)).astype(np.uint8)
-        out[s:e] = _ACGT[two.reshape(-1)[: e - s]]
+        out[s:e] = _BYTE_TO_BASES[w.view(np.uint8)].reshape(-1)[: e - s]
+
+    _parallel(fill, range(0, n, chunk))
     return out
 
 
@@ -212,25 +236,45 @@ def fixed_length_offsets(n_reads: int, length: int) -> np.ndarray:
 
 
 def sample_reads(genome: np.ndarray, n_reads: int, length: int, error_rate: float,
-                 seed: int) -> tuple[np.ndarray, np.ndarray]:
+                 seed: int, chunk: int = 1 << 18) -> tuple[np.ndarray, np.ndarray]:
     """n_reads reads of one length from uniform positions on a random strand,
     each base substituted with probability error_rate (uniform among the
-    other three).  Returns (seq, off)."""
+    other three).  Returns (seq, off).  Generated in chunks of reads; the
+    result does not depend on the chunk size."""
     n = genome.size
-    starts = randint(seed, 41, n_reads, 0, n - length + 1)
-    idx = starts[:, None] + np.arange(length)[None, :]
-    reads = genome[idx]
-    strand = randint(seed, 42, n_reads, 0, 2).astype(bool)
-    if strand.any():
-        reads[strand] = _COMPLEMENT[reads[strand][:, ::-1]]
-    flat = reads.reshape(-1)
-    u = uniform01(seed, 43, 0, flat.size)
-    hit = u < error_rate
-    if hit.any():
-        sub = randint(seed, 44, int(hit.sum()), 1, 4)
-        code = np.searchsorted(_ACGT, flat[hit])
-        flat[hit] = _ACGT[(code + sub) % 4]
-    return flat, fixed_length_offsets(n_reads, length)
+    out = np.empty(n_reads * length, dtype=np.uint8)
+    thr = np.uint64(int(error_rate * 2.0 ** 32))
+    lo32 = np.uint64(0xFFFFFFFF)
+    windows = np.lib.stride_tricks.sliding_window_view(genome, length)
+
+    def one(c0):
+        c1 = min(n_reads, c0 + chunk)
+        m = c1 - c0
+        starts = randint(seed, 41, m, 0, n - length + 1, start=c0)
+        reads = windows[starts]
+        strand = randint(seed, 42, m, 0, 2, start=c0).astype(bool)
+        if strand.any():
+            reads[strand] = _COMPLEMENT[reads[strand][:, ::-1]]
+        flat = reads.reshape(-1)
+        base = c0 * length
+        # base j of the batch is an error iff its 32-bit uniform (one half of
+        # word j // 2) is below the rate; the substitute comes from counter j
+        first = base // 2
+        w = u64(seed, 43, first, (base + flat.size + 1) // 2 - first)
+        halves = np.empty(w.size * 2, dtype=np.uint64)
+        halves[0::2] = w >> np.uint64(32)
+        halves[1::2] = w & lo32
+        halves = halves[base - 2 * first: base - 2 * first + flat.size]
+        idx = np.nonzero(halves < thr)[0]
+        if idx.size:
+            r = u64_at(seed, 44, idx.astype(np.uint64) + np.uint64(base))
+            sub = 1 + (((r >> np.uint64(32)) * np.uint64(3)) >> np.uint64(32)).astype(np.int64)
+            code = np.searchsorted(_ACGT, flat[idx])
+            flat[idx] = _ACGT[(code + sub) % 4]
+        out[base:base + flat.size] = flat
+
+    _parallel(one, range(0, n_reads, chunk))
+    return out, fixed_length_offsets(n_reads, length)
 
 
 def random_reads(n_reads: int, length: int, seed: int) -> tuple[np.ndarray, np.ndarray]:

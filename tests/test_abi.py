@@ -1,0 +1,71 @@
+"""The C ABI library loads and exports every function include/sbf.h declares;
+host-side argument checks work without a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        names += re.findall(r"\b(sbf_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__  # noqa: F401  (build hook lives there)
+    from paper_2606_24417_gb300 import build_lib
+    from paper_2606_24417_gb300.sbf import load_library
+
+    build_lib.build()
+    return load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert "sbf_create" in names and "sbf_query_seqs" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_parameter_validation_without_gpu(lib):
+    from paper_2606_24417_gb300.sbf import SbfError, SuperBloomFilter
+
+    bad = [
+        dict(k=33, m=16, s=28, H=4),
+        dict(k=31, m=0, s=28, H=4),
+        dict(k=31, m=16, s=32, H=4),
+        dict(k=31, m=16, s=28, H=0),
+        dict(k=31, m=16, s=28, H=17),
+        dict(k=31, m=16, s=15, H=4),     # k - s > 15
+        dict(k=31, m=16, s=28, H=4, shard_bits=128),
+        dict(k=31, m=16, s=28, H=4, bits=100),
+    ]
+    for kw in bad:
+        with pytest.raises(SbfError) as ei:
+            SuperBloomFilter(**{"bits": 1 << 20, **kw})
+        assert ei.value.code == -1, kw
+    assert lib.sbf_last_error()
+
+
+def test_num_kmers_host(lib):
+    from paper_2606_24417_gb300.sbf import num_kmers
+
+    off = np.array([0, 10, 10, 50, 80, 111], dtype=np.uint64)
+    assert num_kmers(off, 31) == 0 + 0 + 10 + 0 + 1
+    assert num_kmers(np.array([0], dtype=np.uint64), 31) == 0
+
+
+def test_destroy_null_is_noop(lib):
+    lib.sbf_destroy(None)

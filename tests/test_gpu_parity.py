@@ -1,0 +1,255 @@
+"""GPU parity: libsbf (through the C ABI) against the oracle, bit for bit.
+
+Integer work, so the bar is exact equality of the filter words, of every
+query bit and of every per-read hit count.  Inputs are seeded synthetic
+workloads; sizes span many kernel tiles with ragged tails, and the
+bacterial-genome workload runs at full size with sampled answers checked.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import OracleSBF
+from paper_2606_24417_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_24417_gb300 import build_lib
+
+    build_lib.build()
+    torch.cuda.set_device(0)
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def dev_off(off):
+    return dev(np.asarray(off, dtype=np.uint64).astype(np.int64))
+
+
+def u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def make_filter(k, m, s, H, bits, B=512, canonical=True):
+    from paper_2606_24417_gb300.sbf import SuperBloomFilter
+
+    return SuperBloomFilter(k, m, s, H, bits, shard_bits=B, canonical=canonical)
+
+
+def check_insert_query(params, ins_seq, ins_off, q_seq, q_off, check_stats=True):
+    k, m, s, H, bits, B, canon = params
+    f = make_filter(k, m, s, H, bits, B, canon)
+    o = OracleSBF(k, m, s, H, bits, shard_bits=B, canonical=canon)
+    f.insert(dev(ins_seq), dev_off(ins_off))
+    o.insert(ins_seq, ins_off)
+    assert np.array_equal(f.words(), o.words()), f"words differ for {params}"
+    stats = torch.zeros(3, dtype=torch.int64, device="cuda") if check_stats else None
+    qb, qh = f.query(dev(q_seq), dev_off(q_off), stats=stats)
+    ob, oh = o.query(q_seq, q_off)
+    gb = u32(qb)
+    if not np.array_equal(gb, ob):
+        bad = np.nonzero(gb != ob)[0][:5]
+        raise AssertionError(f"query bits differ for {params} at words {bad}: "
+                             f"{gb[bad]} vs {ob[bad]}")
+    assert np.array_equal(u32(qh), oh), f"hits differ for {params}"
+    if check_stats:
+        valid, runs = o.count_runs(q_seq, q_off)
+        st = stats.cpu().numpy()
+        assert st[0] == valid and st[1] == runs and st[2] == int(oh.sum()), (st, valid, runs)
+    return f, o
+
+
+def ragged_reads(n_reads, seed, genome=None, median=150, sigma=1.2, hi=5000, n_frac=0.0005):
+    """Reads of lognormal lengths (some shorter than k, some empty), part sampled
+    from `genome`, with scattered invalid bytes and lower-case stretches."""
+    lens = synth.lognormal_lengths(n_reads, median, sigma, 0, hi, seed)
+    total = int(lens.sum())
+    seq = synth.uniform_dna(total, seed + 1)
+    if genome is not None:
+        src = synth.randint(seed, 3, n_reads, 0, max(1, genome.size - hi))
+        pos = 0
+        for i, L in enumerate(lens):
+            if i % 2 == 0 and L:
+                seq[pos:pos + L] = genome[src[i]:src[i] + L]
+            pos += L
+    u = synth.uniform01(seed, 5, 0, total)
+    seq[u < n_frac] = ord("N")
+    seq[(u > 0.3) & (u < 0.3 + 0.02)] += 32  # lower case
+    off = np.zeros(n_reads + 1, dtype=np.uint64)
+    np.cumsum(lens, out=off[1:])
+    return seq, off
+
+
+# ---------------------------------------------------------------------------
+# the tiny workload: 1 Mbp uniform random, 2^24 bits in 512-bit shards
+# ---------------------------------------------------------------------------
+def test_tiny_uniform_1mbp_bit_exact():
+    g = synth.uniform_dna(1_000_000, 0)
+    goff = np.array([0, g.size], dtype=np.uint64)
+    other = synth.uniform_dna(1_000_000, 1)
+    q = np.concatenate([g, other])
+    qoff = np.array([0, g.size, q.size], dtype=np.uint64)
+    f, o = check_insert_query((31, 16, 28, 4, 1 << 24, 512, True), g, goff, q, qoff)
+    _, oh = o.query(q, qoff)
+    assert int(oh[0]) == 1_000_000 - 31 + 1   # every inserted k-mer is found
+
+
+PARAMS = [
+    # k, m, s, H, bits, B, canonical
+    (31, 16, 28, 4, 1 << 22, 512, True),
+    (31, 16, 28, 4, 1 << 21, 256, True),
+    (31, 16, 28, 4, 3_000_000, 512, False),
+    (31, 12, 24, 8, 1 << 22, 512, True),
+    (31, 14, 26, 2, 1 << 22, 256, True),
+    (31, 20, 31, 1, 1 << 22, 512, True),
+    (31, 16, 28, 8, 1 << 22, 256, True),
+    (31, 20, 24, 4, 1 << 23, 512, True),
+    (31, 12, 31, 2, 1 << 22, 512, True),
+    (31, 16, 28, 16, 1 << 22, 512, True),   # salted multiply
+    (9, 5, 6, 2, 1 << 16, 256, True),       # Fig. 2 parameters
+    (32, 16, 30, 4, 1 << 22, 512, True),
+    (21, 11, 17, 12, 5000 * 512, 512, True),
+]
+
+
+@pytest.mark.parametrize("params", PARAMS, ids=lambda p: "_".join(map(str, p)))
+def test_ragged_reads_bit_exact(params):
+    genome = synth.uniform_dna(300_000, 7)
+    ins_seq, ins_off = ragged_reads(1500, 11, genome)
+    q_seq, q_off = ragged_reads(2500, 12, genome)
+    check_insert_query(params, ins_seq, ins_off, q_seq, q_off)
+
+
+def test_edge_cases():
+    params = (31, 16, 28, 4, 1 << 20, 512, True)
+    f = make_filter(*params[:5], params[5], params[6])
+    o = OracleSBF(*params[:5], shard_bits=params[5])
+    # empty batch
+    f.insert(dev(np.zeros(0, np.uint8)), dev_off([0]))
+    qb, qh = f.query(dev(np.zeros(0, np.uint8)), dev_off([0]))
+    assert qb.numel() == 0 and qh.numel() == 0
+    # reads shorter than k, exactly k, all-N, separators at every offset
+    g = synth.uniform_dna(5000, 3)
+    reads = [g[:30], g[30:61], np.full(100, ord("N"), np.uint8), g[:0], g[100:131]]
+    for p in range(0, 31, 5):
+        r = g[200:262].copy()
+        r[p] = ord("N")
+        reads.append(r)
+    seq, off = synth.concat(reads)
+    f.insert(dev(seq), dev_off(off))
+    o.insert(seq, off)
+    assert np.array_equal(f.words(), o.words())
+    qb, qh = f.query(dev(seq), dev_off(off))
+    ob, oh = o.query(seq, off)
+    assert np.array_equal(u32(qb), ob) and np.array_equal(u32(qh), oh)
+    assert oh[0] == 0 and oh[1] == 1 and oh[2] == 0 and oh[3] == 0 and oh[4] == 1
+
+
+def test_insert_order_and_repeats_on_gpu():
+    params = (31, 16, 28, 4, 1 << 21, 512, True)
+    seq, off = ragged_reads(3000, 21)
+    f1 = make_filter(*params[:5], params[5], params[6])
+    f1.insert(dev(seq), dev_off(off))
+    # reversed read order, inserted twice
+    lens = np.diff(off.astype(np.int64))
+    reads = [seq[int(off[i]):int(off[i + 1])] for i in range(len(lens))][::-1]
+    s2, o2 = synth.concat(reads)
+    f2 = make_filter(*params[:5], params[5], params[6])
+    f2.insert(dev(s2), dev_off(o2))
+    f2.insert(dev(s2), dev_off(o2))
+    assert np.array_equal(f1.words(), f2.words())
+    # highly repetitive input (contention on few shards)
+    rep = np.tile(synth.uniform_dna(500, 4), 400)
+    check_insert_query(params, rep, np.array([0, rep.size], np.uint64), rep,
+                       np.array([0, rep.size], np.uint64))
+
+
+def test_host_path_matches_device(monkeypatch):
+    params = (31, 16, 28, 4, 1 << 22, 512, True)
+    ins_seq, ins_off = ragged_reads(4000, 31)
+    q_seq, q_off = ragged_reads(6000, 32)
+    monkeypatch.setenv("SBF_HOST_CHUNK_BYTES", "40000")   # many chunk seams
+    f = make_filter(*params[:5], params[5], params[6])
+    f.insert_host(ins_seq, ins_off)
+    o = OracleSBF(*params[:5], shard_bits=params[5])
+    o.insert(ins_seq, ins_off)
+    assert np.array_equal(f.words(), o.words())
+    hb, hh = f.query_host(q_seq, q_off)
+    ob, oh = o.query(q_seq, q_off)
+    assert np.array_equal(hb, ob) and np.array_equal(hh, oh)
+    monkeypatch.delenv("SBF_HOST_CHUNK_BYTES")
+    hb2, hh2 = f.query_host(q_seq, q_off)
+    assert np.array_equal(hb2, ob) and np.array_equal(hh2, oh)
+
+
+def test_checkpoint_roundtrip(tmp_path):
+    params = (31, 16, 28, 4, 1 << 20, 256, False)
+    seq, off = ragged_reads(500, 41)
+    f = make_filter(*params[:5], params[5], params[6])
+    f.insert(dev(seq), dev_off(off))
+    p = tmp_path / "f.sbf"
+    f.save(str(p))
+    g = type(f).load(str(p))
+    assert (g.k, g.m, g.s, g.H, g.shard_bits, g.canonical) == (31, 16, 28, 4, 256, False)
+    assert np.array_equal(f.words(), g.words())
+    qb1, qh1 = f.query(dev(seq), dev_off(off))
+    qb2, qh2 = g.query(dev(seq), dev_off(off))
+    assert torch.equal(qb1, qb2) and torch.equal(qh1, qh2)
+
+
+# ---------------------------------------------------------------------------
+# bacterial-genome workload at full size: 100 Mbp Markov genome with repeats,
+# 2^30-bit filter, 10M sampled reads (1% errors) + 10M random 150 bp reads
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def bacterial():
+    g = synth.bacterial_genome(100_000_000, seed=2)
+    q, qoff = synth.mixed_query_reads(g, 10_000_000, 10_000_000, 150, 0.01, seed=3)
+    return g, q, qoff
+
+
+def test_bacterial_full_size_sampled(bacterial):
+    g, q, qoff = bacterial
+    params = (31, 16, 28, 4, 1 << 30, 512, True)
+    f = make_filter(*params[:5], params[5], params[6])
+    goff = np.array([0, g.size], dtype=np.uint64)
+    dg = dev(g)
+    f.insert(dg, dev_off(goff))
+    o = OracleSBF(*params[:5], shard_bits=params[5])
+    o.insert(g, goff)
+    assert np.array_equal(f.words(), o.words())   # the whole 128 MiB filter
+    # every genome k-mer is positive
+    _, gh = f.query(dg, dev_off(goff), want_bits=False)
+    assert int(u32(gh)[0]) == g.size - 30
+    del dg
+    # the 20M-read query in the launch configuration the benchmark times
+    dq = dev(q)
+    qb, qh = f.query(dq, dev_off(qoff))
+    bits = u32(qb)
+    hits = u32(qh)
+    rng = np.random.default_rng(5)
+    pos = np.sort(rng.choice(q.size, 200_000, replace=False)).astype(np.uint64)
+    want = o.query_positions(q, qoff, pos)
+    got = ((bits[(pos >> np.uint64(5)).astype(np.int64)] >> (pos & np.uint64(31)).astype(np.uint32)) & 1)
+    assert np.array_equal(got.astype(np.uint8), want)
+    reads = np.sort(rng.choice(qoff.size - 1, 3000, replace=False))
+    sub = [q[int(qoff[r]):int(qoff[r + 1])] for r in reads]
+    sseq, soff = synth.concat(sub)
+    _, oh = o.query(sseq, soff)
+    assert np.array_equal(hits[reads], oh)
+    # sampled reads from the genome are mostly positive, random reads almost never
+    n = (qoff.size - 1) // 2
+    assert hits[:n].mean() > 20 and hits[n:].mean() < 0.01
