@@ -107,10 +107,20 @@ def reverse_complement(x: np.ndarray) -> np.ndarray:
     return _COMPLEMENT[np.asarray(x, dtype=np.uint8)[::-1]]
 
 
-def _markov_table(order: int, gc: float, seed: int) -> np.ndarray:
-    """Transition table [4^order, 4]: Dirichlet(1) rows tilted to a stationary GC."""
+# Concentration of the Dirichlet transition rows.  alpha = 5 gives an
+# expected conditional entropy of about 1.9 bits per base, close to real
+# genomes; alpha = 1 (about 1.56 bits) makes 16-mers so repetitive that a
+# few thousand minimizers saturate their shards.
+MARKOV_ALPHA = 5
+
+
+def _markov_table(order: int, gc: float, seed: int, alpha: int = MARKOV_ALPHA) -> np.ndarray:
+    """Transition table [4^order, 4]: Dirichlet(alpha) rows (normalised sums of
+    alpha exponentials) tilted to a stationary GC fraction."""
     n_ctx = 4 ** order
-    e = -np.log1p(-uniform01(seed, 7, 0, n_ctx * 4)).reshape(n_ctx, 4)
+    e = np.zeros((n_ctx, 4))
+    for j in range(alpha):
+        e += -np.log1p(-uniform01(seed, 7 + 100 * j, 0, n_ctx * 4)).reshape(n_ctx, 4)
     base = e / e.sum(axis=1, keepdims=True)
     is_gc = np.array([0.0, 1.0, 1.0, 0.0])
 
@@ -300,7 +310,7 @@ def poisson_arrivals(n: int, rate_per_s: float, seed: int) -> np.ndarray:
 # the evaluation workloads
 # ----------------------------------------------------------------------------
 def bacterial_genome(n: int = 100_000_000, seed: int = 2) -> np.ndarray:
-    """Order-3 Markov genome at GC 50% with 3% of it overwritten by exact
+    """Order-3 Markov genome (Dirichlet(5) rows) at GC 50% with 3% of it overwritten by exact
     1-10 kb repeat copies (random strand)."""
     g = markov_dna(n, 3, 0.5, seed)
     return add_exact_repeats(g, 0.03, 1000, 10000, seed + 100)

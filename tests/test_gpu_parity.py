@@ -252,4 +252,4 @@ def test_bacterial_full_size_sampled(bacterial):
     assert np.array_equal(hits[reads], oh)
     # sampled reads from the genome are mostly positive, random reads almost never
     n = (qoff.size - 1) // 2
-    assert hits[:n].mean() > 20 and hits[n:].mean() < 0.01
+    assert hits[:n].mean() > 20 and hits[n:].mean() < 0.05
