@@ -94,6 +94,11 @@ uint64_t sbf_num_words(const sbf_filter* f);
  * [x*W, (x+1)*W), W = shard_bits / 64).  Owned by the filter. */
 const uint64_t* sbf_device_words(const sbf_filter* f);
 
+/* Which kernels serve this filter: 1 = the fused kernels (compiled grid
+ * w = k-m+1 in {12, 16, 18, 20}, H in {1, 2, 4, 8}), 0 = the generic
+ * one-k-mer-per-thread kernels.  Both give identical bits. */
+int sbf_kernel_variant(const sbf_filter* f);
+
 /* Zero all bits (stream-ordered). */
 int sbf_clear(sbf_filter* f, sbf_stream_t stream);
 

@@ -176,6 +176,8 @@ int sbf_info(const sbf_filter* f, int* k, int* m, int* s, int* H, int* shard_bit
 
 uint64_t sbf_num_words(const sbf_filter* f) { return f ? f->n_words : 0; }
 
+int sbf_kernel_variant(const sbf_filter* f) { return f && f->fused ? 1 : 0; }
+
 const uint64_t* sbf_device_words(const sbf_filter* f) { return f ? f->geom.words : nullptr; }
 
 int sbf_clear(sbf_filter* f, sbf_stream_t stream) {

@@ -1,14 +1,74 @@
-// sbf_fused.cu -- placeholder until the fused kernels land.
-#include "sbf_internal.h"
+// sbf_fused.cu -- dispatch of the fused kernels (sbf_fused.cuh) over the
+// compiled grid: w = k-m+1 in {12 (64-bit order key), 16, 18, 20},
+// H in {1, 2, 4, 8}, shard bits in {256, 512}.  Any other valid parameter
+// set runs the generic kernels with identical results.
+#include "sbf_fused.cuh"
 
 namespace sbf {
-bool fused_supported(const Geom&) { return false; }
-cudaError_t fused_insert(const Geom&, const uint8_t*, uint64_t, const uint64_t*, uint64_t,
-                         cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace fused {
+cudaError_t run_w12(const Params&, int, int, bool, cudaStream_t);
+cudaError_t run_w16(const Params&, int, int, bool, cudaStream_t);
+cudaError_t run_w18(const Params&, int, int, bool, cudaStream_t);
+cudaError_t run_w20(const Params&, int, int, bool, cudaStream_t);
+
+static int window_of(const Geom& g) { return g.k - g.m + 1; }
+
+static bool key64_for(int w) { return w == 12; }
+
+static cudaError_t run(const Params& P, bool insert, cudaStream_t st) {
+  switch (window_of(P.g)) {
+    case 12: return run_w12(P, P.g.H, P.g.shard_bits, insert, st);
+    case 16: return run_w16(P, P.g.H, P.g.shard_bits, insert, st);
+    case 18: return run_w18(P, P.g.H, P.g.shard_bits, insert, st);
+    case 20: return run_w20(P, P.g.H, P.g.shard_bits, insert, st);
+    default: return cudaErrorNotSupported;
+  }
 }
-cudaError_t fused_query(const Geom&, const uint8_t*, uint64_t, const uint64_t*, uint64_t, uint32_t*,
-                        uint32_t*, uint64_t*, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+static uint64_t iterations(const Geom& g, uint64_t seq_len) {
+  int w = window_of(g);
+  int adv = (15 + w - 1 >= 32 ? 30 : 31) * kLanePos;
+  return (seq_len + adv - 1) / adv;
 }
+
+}  // namespace fused
+
+bool fused_supported(const Geom& g) {
+  if (getenv("SBF_FORCE_GENERIC")) return false;
+  if (g.k < 2 || g.k > 32) return false;
+  int w = fused::window_of(g);
+  if (w != 12 && w != 16 && w != 18 && w != 20) return false;
+  if ((2 * g.m > 32) != fused::key64_for(w)) return false;
+  if (g.H != 1 && g.H != 2 && g.H != 4 && g.H != 8) return false;
+#ifdef SBF_MINIMAL_GRID
+  if (w != 16 || g.H != 4) return false;
+#endif
+  return g.shard_bits == 256 || g.shard_bits == 512;
+}
+
+cudaError_t fused_insert(const Geom& g, const uint8_t* seq, uint64_t seq_len, const uint64_t* off,
+                         uint64_t n_reads, cudaStream_t st) {
+  if (seq_len == 0 || n_reads == 0) return cudaSuccess;
+  fused::Params P{g, seq, seq_len, off, n_reads, nullptr, nullptr, nullptr,
+                  fused::iterations(g, seq_len)};
+  return fused::run(P, true, st);
+}
+
+cudaError_t fused_query(const Geom& g, const uint8_t* seq, uint64_t seq_len, const uint64_t* off,
+                        uint64_t n_reads, uint32_t* bits, uint32_t* hits, uint64_t* stats,
+                        cudaStream_t st) {
+  cudaError_t e;
+  if (bits && seq_len) {
+    e = cudaMemsetAsync(bits, 0, ((seq_len + 31) / 32) * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+  }
+  if (hits && n_reads) {
+    e = cudaMemsetAsync(hits, 0, n_reads * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+  }
+  if (seq_len == 0 || n_reads == 0) return cudaSuccess;
+  fused::Params P{g, seq, seq_len, off, n_reads, bits, hits, stats, fused::iterations(g, seq_len)};
+  return fused::run(P, false, st);
+}
+
 }  // namespace sbf

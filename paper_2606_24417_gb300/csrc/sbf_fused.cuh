@@ -1,0 +1,787 @@
+// sbf_fused.cuh -- fused sequence-native insert / query kernels for sm_103a.
+//
+// What they compute is Alg. 1 (insert) and Alg. 2 (query) of the cuSBF
+// paper; how is designed for GB300 rather than taken from the paper:
+//
+//  * Warp-private pipeline, no block-wide barriers.  A warp owns a contiguous
+//    range of start positions and walks it in iterations of U*16 positions
+//    (U = 31 or 30 "useful" lanes; the last lane(s) only compute values their
+//    left neighbours need).
+//  * Staging: each lane loads 16 raw bytes (one 128-bit non-coherent load),
+//    encodes them ONCE into a 2-bit word (first base most significant), its
+//    reverse complement and a 16-bit invalid-base mask in shared memory.
+//  * Lane chunks: lane l owns positions [16l, 16l+16).  From three staged words
+//    it extracts every m-mer and s-mer by static funnel shifts (no per-k-mer
+//    re-packing, Sec. IV-C / IV-E amortisation taken to the whole chunk).
+//  * Minimizer: the sliding minimum of the order keys over w windows is the
+//    van Herk / Gil-Werman block decomposition over the lane's keys and its
+//    neighbour's (shuffled).  The order key is a bijection, so the minimizer
+//    value is recovered from the minimum key by one multiplication with the
+//    modular inverse -- no argmin is tracked.
+//  * Runs (super-k-mers, Sec. II-B): run heads are compacted warp-wide into
+//    slots; the shard of each run is computed once and loaded once into
+//    shared memory with cp.async (query), or zeroed there (insert).
+//  * Findere with pair deduplication: k-mer j needs its k-s+1 s-mers tested
+//    in its run's shard.  Every position t tests its own pair (t, shard(t));
+//    every run end e adds the z = k-s pairs (e+d, shard(e)).  A word-parallel
+//    sliding AND inside runs plus a kill mask from the extra pairs gives the
+//    Findere answers bit-packed, without any per-k-mer re-hashing.
+//  * Insert ORs the same pairs' bits into the run's slot (shared atomics) and
+//    flushes each slot with coalesced 64-bit atomicOr (Alg. 1's head-only
+//    atomics, one per word per run).
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include "sbf_internal.h"
+
+namespace sbf {
+namespace fused {
+
+constexpr int kLanePos = 16;        // start positions per lane
+constexpr int kWarps = 4;           // warps per block
+constexpr int kThreads = 32 * kWarps;
+constexpr int kSlotCap = 96;        // runs per iteration with a shard copy in shared memory
+constexpr int kStage = 34;          // staged 16-base words per iteration (544 bases)
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Modular inverses of the odd golden-ratio multipliers (Newton iteration).
+__host__ __device__ constexpr uint32_t inv32(uint32_t a) {
+  uint32_t x = a;
+  for (int i = 0; i < 5; ++i) x *= 2u - a * x;
+  return x;
+}
+__host__ __device__ constexpr uint64_t inv64(uint64_t a) {
+  uint64_t x = a;
+  for (int i = 0; i < 6; ++i) x *= 2ull - a * x;
+  return x;
+}
+static_assert(inv32(kGolden32) * kGolden32 == 1u, "inverse");
+static_assert(inv64(kGolden64) * kGolden64 == 1ull, "inverse");
+
+template <int W>
+struct Shape {
+  // lanes whose chunk is only read by neighbours: windows reach up to
+  // position 15 + W - 1 of the chunk, i.e. into lane l+1 (W <= 17) or l+2
+  static constexpr int kHelpers = (15 + W - 1 >= 32) ? 2 : 1;
+  static constexpr int kUseful = 32 - kHelpers;
+  static constexpr int kAdvance = kUseful * kLanePos;
+};
+
+// Bit-address packs: H in-shard addresses of one s-mer, one per byte (H <= 4)
+// or the masked hash itself (H = 8).
+template <int H, int B>
+struct Layout {
+  static constexpr int W64 = B / 64;
+  static constexpr int S = H < W64 ? H : W64;       // sectors (H is a power of two)
+  static constexpr int SB = B / S;                   // sector bits
+  static constexpr int b = (SB == 64) ? 6 : (SB == 128) ? 7 : (SB == 256) ? 8 : 9;
+  static constexpr int q = 64 / H;                   // slice width (>= b for H <= 8)
+  static constexpr int W32 = B / 32;                 // 32-bit words per shard
+  static constexpr int SW32 = SB / 32;               // 32-bit words per sector
+  using Pack = typename std::conditional<(H == 8), uint64_t, uint32_t>::type;
+  static_assert(q >= b, "bit-slicing only");
+};
+
+template <int H, int B>
+__device__ __forceinline__ typename Layout<H, B>::Pack make_pack(uint64_t h) {
+  using L = Layout<H, B>;
+  const uint32_t lo = (uint32_t)h, hi = (uint32_t)(h >> 32);
+  constexpr uint32_t m = (1u << L::b) - 1u;
+  if constexpr (H == 1) {
+    return lo & m;
+  } else if constexpr (H == 2) {
+    return __byte_perm(lo, hi, 0x0040) & (m | (m << 8));
+  } else if constexpr (H == 4) {
+    return __byte_perm(lo, hi, 0x6420) & (m * 0x01010101u);
+  } else {
+    return h & ((uint64_t)m * 0x0101010101010101ull);
+  }
+}
+
+template <int H, int B>
+__device__ __forceinline__ uint32_t pack_addr(typename Layout<H, B>::Pack pk, int i) {
+  if constexpr (H == 1) {
+    return (uint32_t)pk;
+  } else if constexpr (H == 8) {
+    return (uint32_t)(pk >> (8 * i)) & 0xFFu;
+  } else {
+    return ((uint32_t)pk >> (8 * i)) & 0xFFu;
+  }
+}
+
+struct Params {
+  Geom g;
+  const uint8_t* seq;
+  uint64_t seq_len;
+  const uint64_t* off;
+  uint64_t n_reads;
+  uint32_t* bits;     // query: bit-packed answers (zeroed by the launcher)
+  uint32_t* hits;     // query: per-read counts (zeroed by the launcher)
+  uint64_t* stats;    // query: valid k-mers, runs, positives (may be NULL)
+  uint64_t iters;     // total iterations over the sequence
+};
+
+template <int H, int B>
+struct alignas(16) WarpSmem {
+  using L = Layout<H, B>;
+  using Pack = typename L::Pack;
+  static constexpr int kHsStride = sizeof(Pack) == 4 ? 34 : 33;  // bank-conflict-free transposes
+  uint32_t shard[kSlotCap * L::W32];     // shard copies (query) or masks (insert)
+  uint64_t slot_x[512];                  // minimizer key, then shard index, per slot
+  Pack hs[kLanePos * kHsStride];         // s-mer bit-address packs, [j][lane]
+  uint16_t slot_of[512];                 // slot of each valid position
+  uint16_t end_list[512];                // run-end positions
+  uint16_t slot_head[512];               // run-head position of each slot
+  uint32_t fwd[kStage];                  // staged 2-bit words
+  uint32_t rcw[kStage];                  // their reverse complements
+  uint32_t bad[kStage];                  // 16-bit invalid masks
+  uint32_t valid_w[17];                  // position-space bit words (+1 zero word)
+  uint32_t end_w[17];
+  uint32_t own_w[17];
+  uint32_t kill_w[17];
+  uint32_t k_w[17];
+  uint32_t pref_w[17];
+};
+
+__device__ __forceinline__ uint32_t pairswap(uint32_t x) {
+  return ((x >> 1) & 0x55555555u) | ((x & 0x55555555u) << 1);
+}
+
+// 16 bytes at pos (bytes past seq_len read as 'N').
+__device__ __forceinline__ uint4 load16(const uint8_t* seq, uint64_t pos, uint64_t seq_len,
+                                        bool aligned) {
+  if (aligned && pos + 16 <= seq_len) return __ldg(reinterpret_cast<const uint4*>(seq + pos));
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      uint64_t p = pos + 4 * i + b;
+      uint32_t ch = p < seq_len ? (uint32_t)seq[p] : (uint32_t)'N';
+      v |= ch << (8 * b);
+    }
+    w[i] = v;
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Encode 4 ASCII bytes: 8-bit group of 2-bit codes (byte 0 most significant)
+// and a 4-bit invalid mask (bit b = byte b not A/C/G/T in either case).
+__device__ __forceinline__ void encode4(uint32_t x, uint32_t& code8, uint32_t& bad4) {
+  uint32_t t = ((x >> 1) ^ (x >> 2)) & 0x03030303u;
+  code8 = (t * 0x40100401u) >> 24;
+  uint32_t sel = (t & 0x3u) | ((t >> 4) & 0x30u) | ((t >> 8) & 0x300u) | ((t >> 12) & 0x3000u);
+  uint32_t expect = __byte_perm(0x54474341u, 0u, sel);  // 'A','C','G','T' by code
+  uint32_t diff = expect ^ (x & 0xDFDFDFDFu);            // 0 byte <=> valid
+  uint32_t nz = (((diff & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | diff) & 0x80808080u;
+  bad4 = ((nz >> 7) * 0x00204081u >> 21) & 0xFu;
+}
+
+// Read the warp's position range [lo, hi) of start positions holding the
+// reads: last r with off[r] <= p (32-ary search, warp-uniform result).
+__device__ __forceinline__ uint64_t warp_find_read(const uint64_t* off, uint64_t n_reads,
+                                                   uint64_t p, int lane) {
+  uint64_t lo = 0, hi = n_reads;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    uint64_t step = (hi - lo + 31) / 32;
+    uint64_t c = lo + (uint64_t)lane * step;
+    bool pred = c < hi && off[c] <= p;
+    unsigned bal = __ballot_sync(kFull, pred);
+    if (bal == 0) return lo;  // off[lo] > p: before the first read
+    int i = 31 - __clz(bal);
+    uint64_t nlo = lo + (uint64_t)i * step;
+    uint64_t nhi = nlo + step < hi ? nlo + step : hi;
+    lo = nlo;
+    hi = nhi;
+  }
+  return lo;
+}
+
+template <typename KeyT>
+__device__ __forceinline__ KeyT key_of(uint64_t v) {
+  if constexpr (sizeof(KeyT) == 4) {
+    return (uint32_t)v * kGolden32;
+  } else {
+    return v * kGolden64;
+  }
+}
+
+// Minimizer order key and validity of the k-mer at position p, straight from
+// global memory (only for exact run-head statistics at a warp's first position).
+template <typename KeyT>
+__device__ bool prev_kmer_key(const Geom& g, const uint8_t* seq, uint64_t seq_len,
+                              const uint64_t* off, uint64_t n_reads, uint64_t p, KeyT& key) {
+  if (n_reads == 0) return false;
+  uint64_t lo = 0, hi = n_reads;
+  while (hi - lo > 1) {
+    uint64_t mid = lo + ((hi - lo) >> 1);
+    if (off[mid] <= p) lo = mid; else hi = mid;
+  }
+  uint64_t end = off[lo + 1] < seq_len ? off[lo + 1] : seq_len;
+  if (off[lo] > p || p + (uint64_t)g.k > end) return false;
+  uint64_t fwd = 0, rc = 0;
+  for (int i = 0; i < g.k; ++i) {
+    uint32_t ch = seq[p + i];
+    if (!base_valid(ch)) return false;
+    uint32_t c = base_code(ch);
+    fwd = (fwd << 2) | c;
+    rc |= (uint64_t)(3u - c) << (2 * i);
+  }
+  KeyT best = 0;
+  for (int i = 0; i <= g.k - g.m; ++i) {
+    uint64_t f = (fwd >> (2 * (g.k - g.m - i))) & len_mask(g.m);
+    uint64_t r = (rc >> (2 * i)) & len_mask(g.m);
+    uint64_t v = g.canonical ? (f < r ? f : r) : f;
+    KeyT kk = key_of<KeyT>(v);
+    if (i == 0 || kk < best) best = kk;
+  }
+  key = best;
+  return true;
+}
+
+template <int W, int H, int B, bool KEY64, bool INSERT>
+__global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
+  using L = Layout<H, B>;
+  using Pack = typename L::Pack;
+  using KeyT = typename std::conditional<KEY64, uint64_t, uint32_t>::type;
+  using Sm = WarpSmem<H, B>;
+  constexpr int U = Shape<W>::kUseful;
+  constexpr int ADV = Shape<W>::kAdvance;
+  constexpr int HS = Sm::kHsStride;
+
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  Sm& S = reinterpret_cast<Sm*>(smem_raw)[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const Geom& g = P.g;
+  const int k = g.k, m = g.m, s = g.s, z = g.k - g.s;
+  const bool canon = g.canonical != 0;
+
+  // contiguous share of iterations for this warp
+  const uint64_t tw = (uint64_t)gridDim.x * kWarps;
+  const uint64_t gw = (uint64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const uint64_t per = P.iters / tw, rem = P.iters % tw;
+  const uint64_t it0 = gw * per + (gw < rem ? gw : rem);
+  const uint64_t it1 = it0 + per + (gw < rem ? 1 : 0);
+  if (it0 >= it1) return;
+
+  const uint64_t seq_len = P.seq_len;
+  const uint64_t* off = P.off;
+  const uint64_t n_reads = P.n_reads;
+  // start positions outside [lo_pos, hi_pos) belong to no read
+  uint64_t lo_pos = 0, hi_pos = 0;
+  if (n_reads > 0) {
+    lo_pos = off[0] < seq_len ? off[0] : seq_len;
+    hi_pos = off[n_reads] < seq_len ? off[n_reads] : seq_len;
+  }
+  const bool aligned = (reinterpret_cast<uintptr_t>(P.seq) & 15u) == 0;
+  const uint64_t smask = (s >= 32) ? ~0ull : ((1ull << (2 * s)) - 1ull);
+  const uint64_t mmask = (m >= 32) ? ~0ull : ((1ull << (2 * m)) - 1ull);
+  uint32_t* words32 = reinterpret_cast<uint32_t*>(g.words);
+
+  uint64_t p0 = it0 * (uint64_t)ADV;
+  uint64_t r_cur = n_reads > 0 ? warp_find_read(off, n_reads, p0, lane) : 0;
+
+  // run-head carry: validity and minimizer key of position p0 - 1
+  bool carry_valid = false;
+  KeyT carry_key = 0;
+  if (!INSERT && P.stats && p0 > 0) {
+    KeyT kk = 0;
+    bool v = false;
+    if (lane == 0) v = prev_kmer_key<KeyT>(g, P.seq, seq_len, off, n_reads, p0 - 1, kk);
+    carry_valid = __shfl_sync(kFull, v, 0);
+    if constexpr (KEY64) {
+      carry_key = ((uint64_t)__shfl_sync(kFull, (uint32_t)(kk >> 32), 0) << 32) |
+                  __shfl_sync(kFull, (uint32_t)kk, 0);
+    } else {
+      carry_key = __shfl_sync(kFull, kk, 0);
+    }
+  }
+  unsigned long long st_valid = 0, st_runs = 0, st_pos = 0;
+
+  for (uint64_t it = it0; it < it1; ++it, p0 += ADV) {
+    // ---------------- staging: encode 544 bases once ----------------------
+    for (int wi = lane; wi < kStage; wi += 32) {
+      uint64_t pos = p0 + 16ull * wi;
+      uint4 raw = load16(P.seq, pos, seq_len, aligned);
+      uint32_t c8, b4, fw = 0, bad = 0;
+      encode4(raw.x, c8, b4); fw = c8;             bad = b4;
+      encode4(raw.y, c8, b4); fw = (fw << 8) | c8; bad |= b4 << 4;
+      encode4(raw.z, c8, b4); fw = (fw << 8) | c8; bad |= b4 << 8;
+      encode4(raw.w, c8, b4); fw = (fw << 8) | c8; bad |= b4 << 12;
+      if (pos < lo_pos || pos + 16 > hi_pos) {  // outside the reads' span
+        uint32_t okm = 0;
+#pragma unroll
+        for (int b = 0; b < 16; ++b) okm |= (uint32_t)(pos + b >= lo_pos && pos + b < hi_pos) << b;
+        bad |= ~okm & 0xFFFFu;
+      }
+      S.fwd[wi] = fw;
+      S.rcw[wi] = ~pairswap(__brev(fw));
+      S.bad[wi] = bad;
+    }
+    if (lane < 17) {
+      S.kill_w[lane] = 0;
+      S.own_w[lane] = 0;
+    }
+    __syncwarp();
+
+    const uint64_t Pl = p0 + 16ull * lane;
+    const uint32_t F0 = S.fwd[lane], F1 = S.fwd[lane + 1], F2 = S.fwd[lane + 2];
+    const uint32_t R0 = S.rcw[lane + 2], R1 = S.rcw[lane + 1], R2 = S.rcw[lane];
+    const uint64_t bad48 = (uint64_t)S.bad[lane] | ((uint64_t)S.bad[lane + 1] << 16) |
+                           ((uint64_t)S.bad[lane + 2] << 32);
+
+    // ---------------- read ends inside the window; cursor advance --------
+    uint64_t E48 = 0;
+    uint64_t adv = 0;
+    {
+      const uint64_t win_hi = p0 + 16ull * kStage, own_hi = p0 + ADV;
+      uint64_t q0 = r_cur;
+      while (true) {
+        uint64_t q = q0 + lane;
+        uint64_t e = ~0ull;
+        if (q < n_reads) {
+          e = off[q + 1];
+          if (e > seq_len) e = seq_len;
+        }
+        unsigned bw = __ballot_sync(kFull, e < win_hi);
+        adv += __popc(__ballot_sync(kFull, e <= own_hi));
+        unsigned bb = bw;
+        while (bb) {
+          int i = __ffs(bb) - 1;
+          bb &= bb - 1;
+          uint64_t ei = __shfl_sync(kFull, e, i);
+          int64_t d = (int64_t)ei - 1 - (int64_t)Pl;   // last base of that read
+          if (d >= 0 && d < 48) E48 |= 1ull << d;
+        }
+        if (bw != kFull) break;
+        q0 += 32;
+      }
+    }
+
+    // ---------------- validity of the lane's 16 k-mers --------------------
+    uint32_t valid16;
+    {
+      // invalid(j) <=> an invalid base in [j, j+k-1] or a read's last base in [j, j+k-2]
+      uint64_t X = bad48 | (bad48 >> 1) | E48;
+      int len = 1;
+      while (2 * len <= k - 1) {
+        X |= X >> len;
+        len *= 2;
+      }
+      X |= X >> (k - 1 - len);
+      valid16 = (uint32_t)(~X) & 0xFFFFu;
+      if (lane >= U) valid16 = 0;
+    }
+
+    // ---------------- per position: s-mer packs and m-mer keys ------------
+    KeyT key[kLanePos];
+#pragma unroll
+    for (int j = 0; j < kLanePos; ++j) {
+      const uint32_t hi = __funnelshift_l(F1, F0, 2 * j);
+      const uint32_t lo = __funnelshift_l(F2, F1, 2 * j);
+      const uint32_t rlo = __funnelshift_r(R2, R1, 2 * j);
+      const uint32_t rhi = __funnelshift_r(R1, R0, 2 * j);
+      const uint64_t x64 = ((uint64_t)hi << 32) | lo;
+      const uint64_t r64 = ((uint64_t)rhi << 32) | rlo;
+      uint64_t fs = x64 >> (64 - 2 * s);
+      uint64_t rs = r64 & smask;
+      uint64_t cs = (canon && rs < fs) ? rs : fs;
+      S.hs[j * HS + lane] = make_pack<H, B>(mix64(cs ^ kSmerKey));
+      if constexpr (KEY64) {
+        uint64_t fm = x64 >> (64 - 2 * m);
+        uint64_t rm = r64 & mmask;
+        uint64_t cm = (canon && rm < fm) ? rm : fm;
+        key[j] = cm * kGolden64;
+      } else {
+        uint32_t fm = hi >> (32 - 2 * m);
+        uint32_t rm = rlo & (uint32_t)mmask;
+        uint32_t cm = (canon && rm < fm) ? rm : fm;
+        key[j] = cm * kGolden32;
+      }
+    }
+
+    // ---------------- sliding minimum over W windows (van Herk) -----------
+    constexpr int NE = 15 + W;  // positions 0 .. 15+W-1 of the extended chunk
+    KeyT ext[NE];
+#pragma unroll
+    for (int i = 0; i < NE; ++i) {
+      if (i < 16) {
+        ext[i] = key[i];
+      } else if (i < 32) {
+        if constexpr (KEY64) {
+          uint32_t h = __shfl_down_sync(kFull, (uint32_t)(key[i - 16] >> 32), 1);
+          uint32_t l = __shfl_down_sync(kFull, (uint32_t)key[i - 16], 1);
+          ext[i] = ((uint64_t)h << 32) | l;
+        } else {
+          ext[i] = __shfl_down_sync(kFull, key[i - 16], 1);
+        }
+      } else {
+        if constexpr (KEY64) {
+          uint32_t h = __shfl_down_sync(kFull, (uint32_t)(key[i - 32] >> 32), 2);
+          uint32_t l = __shfl_down_sync(kFull, (uint32_t)key[i - 32], 2);
+          ext[i] = ((uint64_t)h << 32) | l;
+        } else {
+          ext[i] = __shfl_down_sync(kFull, key[i - 32], 2);
+        }
+      }
+    }
+    KeyT mk[kLanePos];
+    {
+      // blocks [0, W), [W, 2W), ...: suffix minima inside each block and
+      // prefix minima inside each block; window [j, j+W-1] = suffix(j) and
+      // prefix(j+W-1) of the next block.
+      KeyT suf[NE], pre[NE];
+#pragma unroll
+      for (int i = NE - 1; i >= 0; --i) {
+        if (i == NE - 1 || i % W == W - 1) {
+          suf[i] = ext[i];
+        } else {
+          suf[i] = ext[i] < suf[i + 1] ? ext[i] : suf[i + 1];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NE; ++i) {
+        if (i % W == 0) {
+          pre[i] = ext[i];
+        } else {
+          pre[i] = ext[i] < pre[i - 1] ? ext[i] : pre[i - 1];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kLanePos; ++j) {
+        if (j % W == 0) {
+          mk[j] = suf[j];
+        } else {
+          KeyT a = suf[j], b = pre[j + W - 1];
+          mk[j] = a < b ? a : b;
+        }
+      }
+    }
+
+    // ---------------- run heads / ends ------------------------------------
+    uint32_t eq_prev = 0;  // bit j: mk[j] == mk[j-1] (bit 0: vs previous lane)
+#pragma unroll
+    for (int j = 1; j < kLanePos; ++j) eq_prev |= (uint32_t)(mk[j] == mk[j - 1]) << j;
+    KeyT prev_mk, next_mk;
+    if constexpr (KEY64) {
+      prev_mk = ((uint64_t)__shfl_up_sync(kFull, (uint32_t)(mk[15] >> 32), 1) << 32) |
+                __shfl_up_sync(kFull, (uint32_t)mk[15], 1);
+      next_mk = ((uint64_t)__shfl_down_sync(kFull, (uint32_t)(mk[0] >> 32), 1) << 32) |
+                __shfl_down_sync(kFull, (uint32_t)mk[0], 1);
+    } else {
+      prev_mk = __shfl_up_sync(kFull, mk[15], 1);
+      next_mk = __shfl_down_sync(kFull, mk[0], 1);
+    }
+    uint32_t prev_valid = (__shfl_up_sync(kFull, valid16, 1) >> 15) & 1u;
+    uint32_t next_valid = __shfl_down_sync(kFull, valid16, 1) & 1u;
+    if (lane == 0) {
+      prev_valid = carry_valid ? 1u : 0u;
+      prev_mk = carry_key;
+    }
+    eq_prev |= (uint32_t)(prev_mk == mk[0]);
+    const uint32_t vprev = ((valid16 << 1) | prev_valid) & 0xFFFFu;
+    const uint32_t head16 = valid16 & ~(vprev & eq_prev);
+    const uint32_t eq_next = (eq_prev >> 1) | ((uint32_t)(mk[15] == next_mk) << 15);
+    const uint32_t vnext = ((valid16 >> 1) | (next_valid << 15)) & 0xFFFFu;
+    uint32_t end16 = valid16 & ~(vnext & eq_next);
+    if (lane == U - 1) end16 |= valid16 & 0x8000u;  // iteration end closes every run
+    const uint32_t slot16 = head16 | (lane == 0 ? (valid16 & 1u) : 0u);
+    // carry for the next iteration: position p0 + ADV - 1 = lane U-1, j = 15
+    {
+      uint32_t cv = __shfl_sync(kFull, valid16 >> 15, U - 1) & 1u;
+      KeyT ck;
+      if constexpr (KEY64) {
+        ck = ((uint64_t)__shfl_sync(kFull, (uint32_t)(mk[15] >> 32), U - 1) << 32) |
+             __shfl_sync(kFull, (uint32_t)mk[15], U - 1);
+      } else {
+        ck = __shfl_sync(kFull, mk[15], U - 1);
+      }
+      carry_valid = cv != 0;
+      carry_key = ck;
+    }
+    if (!INSERT && P.stats) {
+      st_valid += __popc(valid16);
+      st_runs += __popc(head16);
+    }
+
+    // ---------------- slots: one per run piece ----------------------------
+    uint32_t n_slot = __popc(slot16), n_end = __popc(end16);
+    uint32_t slot_base = n_slot, end_base = n_end;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      uint32_t a = __shfl_up_sync(kFull, slot_base, d);
+      uint32_t b = __shfl_up_sync(kFull, end_base, d);
+      if (lane >= d) {
+        slot_base += a;
+        end_base += b;
+      }
+    }
+    const uint32_t total_slots = __shfl_sync(kFull, slot_base, 31);
+    const uint32_t total_ends = __shfl_sync(kFull, end_base, 31);
+    slot_base -= n_slot;
+    end_base -= n_end;
+    {
+      uint32_t sl = slot_base - 1u, en = end_base;
+#pragma unroll
+      for (int j = 0; j < kLanePos; ++j) {
+        const uint32_t t = 16u * lane + j;
+        if ((slot16 >> j) & 1u) {
+          ++sl;
+          S.slot_x[sl] = (uint64_t)mk[j];
+          S.slot_head[sl] = (uint16_t)t;
+        }
+        if ((valid16 >> j) & 1u) S.slot_of[t] = (uint16_t)sl;
+        if ((end16 >> j) & 1u) S.end_list[en++] = (uint16_t)t;
+      }
+    }
+    reinterpret_cast<uint16_t*>(S.valid_w)[lane] = (uint16_t)valid16;
+    reinterpret_cast<uint16_t*>(S.end_w)[lane] = (uint16_t)end16;
+    if (lane == 0) {
+      S.valid_w[16] = 0;
+      S.end_w[16] = 0;
+    }
+    __syncwarp();
+
+    // ---------------- shards of the runs ----------------------------------
+    const uint64_t n_shards = g.n_shards;
+    for (uint32_t si = lane; si < total_slots; si += 32) {
+      uint64_t mu;
+      if constexpr (KEY64) {
+        mu = S.slot_x[si] * inv64(kGolden64);
+      } else {
+        mu = (uint32_t)S.slot_x[si] * inv32(kGolden32);
+      }
+      uint64_t x = __umul64hi(mix64(mu ^ kShardKey), n_shards);
+      S.slot_x[si] = x;
+      if (si < (uint32_t)kSlotCap) {
+        if constexpr (INSERT) {
+#pragma unroll
+          for (int w = 0; w < L::W32; w += 4)
+            *reinterpret_cast<uint4*>(&S.shard[si * L::W32 + w]) = make_uint4(0, 0, 0, 0);
+        } else {
+          const uint8_t* src = reinterpret_cast<const uint8_t*>(g.words) + x * (uint64_t)(B / 8);
+          uint32_t dst = (uint32_t)__cvta_generic_to_shared(&S.shard[si * L::W32]);
+#pragma unroll
+          for (int c = 0; c < B / 128; ++c)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16 * c),
+                         "l"(src + 16 * c));
+        }
+      }
+    }
+    if constexpr (!INSERT) {
+      asm volatile("cp.async.commit_group;\n" ::);
+      asm volatile("cp.async.wait_group 0;\n" ::);
+    }
+    __syncwarp();
+
+    // ---------------- own pairs: (t, shard(t)) ----------------------------
+    auto word_of = [&](uint32_t slot, uint32_t widx) -> uint32_t {
+      if (slot < (uint32_t)kSlotCap) return S.shard[slot * L::W32 + widx];
+      return __ldg(words32 + S.slot_x[slot] * (uint64_t)L::W32 + widx);
+    };
+    auto test_pair = [&](Pack pk, uint32_t slot) -> bool {
+      uint32_t acc = 1u;
+#pragma unroll
+      for (int i = 0; i < H; ++i) {
+        const uint32_t p = pack_addr<H, B>(pk, i);
+        const uint32_t widx = (uint32_t)(i % L::S) * L::SW32 + (p >> 5);
+        const uint32_t w = word_of(slot, widx);
+        acc &= __funnelshift_r(w, w, p);
+      }
+      return acc & 1u;
+    };
+    auto set_pair = [&](Pack pk, uint32_t slot) {
+#pragma unroll
+      for (int i = 0; i < H; ++i) {
+        const uint32_t p = pack_addr<H, B>(pk, i);
+        const uint32_t widx = (uint32_t)(i % L::S) * L::SW32 + (p >> 5);
+        const uint32_t bit = 1u << (p & 31u);
+        if (slot < (uint32_t)kSlotCap) {
+          atomicOr(&S.shard[slot * L::W32 + widx], bit);
+        } else {
+          atomicOr(&words32[S.slot_x[slot] * (uint64_t)L::W32 + widx], bit);
+        }
+      }
+    };
+
+#pragma unroll 1
+    for (int pass = 0; pass < 16; ++pass) {
+      const uint32_t t = 32u * pass + lane;
+      const bool v = (S.valid_w[pass] >> lane) & 1u;
+      bool ok = false;
+      if (v) {
+        const Pack pk = S.hs[(t & 15u) * HS + (t >> 4)];
+        const uint32_t slot = S.slot_of[t];
+        if constexpr (INSERT) {
+          set_pair(pk, slot);
+        } else {
+          ok = test_pair(pk, slot);
+        }
+      }
+      if constexpr (!INSERT) {
+        const unsigned own = __ballot_sync(kFull, ok);
+        if (lane == 0) S.own_w[pass] = own;
+      }
+    }
+
+    // ---------------- extra pairs after each run end: (e+d, shard(e)) ----
+#pragma unroll 1
+    for (int d = 1; d <= z; ++d) {
+      for (uint32_t ei = lane; ei < total_ends; ei += 32) {
+        const uint32_t e = S.end_list[ei];
+        const uint32_t t = e + d;
+        const uint32_t slot = S.slot_of[e];
+        const Pack pk = S.hs[(t & 15u) * HS + (t >> 4)];
+        if constexpr (INSERT) {
+          set_pair(pk, slot);
+        } else {
+          if (!test_pair(pk, slot)) {
+            // k-mers [max(t - z, run head), e] of this run need s-mer t
+            int lo = (int)t - z;
+            const int hd = S.slot_head[slot];
+            if (lo < hd) lo = hd;
+            const uint32_t w1 = (uint32_t)lo >> 5, w2 = e >> 5;
+            const uint32_t bl = (uint32_t)lo & 31u, bh = e & 31u;
+            if (w1 == w2) {
+              atomicOr(&S.kill_w[w1], (0xFFFFFFFFu >> (31u - bh)) & (0xFFFFFFFFu << bl));
+            } else {
+              atomicOr(&S.kill_w[w1], 0xFFFFFFFFu << bl);
+              atomicOr(&S.kill_w[w2], 0xFFFFFFFFu >> (31u - bh));
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();
+
+    if constexpr (INSERT) {
+      // ---------------- flush run masks: coalesced 64-bit atomics ----------
+      const uint32_t n_mem = total_slots < (uint32_t)kSlotCap ? total_slots : (uint32_t)kSlotCap;
+      const uint32_t n_words = n_mem * (B / 64);
+      const uint64_t* sm64 = reinterpret_cast<const uint64_t*>(S.shard);
+      for (uint32_t i = lane; i < n_words; i += 32) {
+        const uint32_t si = i / (B / 64), wd = i % (B / 64);
+        const uint64_t v = sm64[i];
+        if (v)
+          atomicOr(reinterpret_cast<unsigned long long*>(g.words) + S.slot_x[si] * (uint64_t)(B / 64) + wd,
+                   (unsigned long long)v);
+      }
+      __syncwarp();
+    } else {
+      // ---------------- Findere AND inside runs -> answer words -----------
+      if (lane < 16) {
+        const uint64_t O64 = (uint64_t)S.own_w[lane] | ((uint64_t)S.own_w[lane + 1] << 32);
+        const uint64_t E64 = (uint64_t)S.end_w[lane] | ((uint64_t)S.end_w[lane + 1] << 32);
+        uint64_t res = O64, c = 0;
+        for (int d = 1; d <= z; ++d) {
+          c |= E64 >> (d - 1);
+          res &= (O64 >> d) | c;
+        }
+        const uint32_t K = (uint32_t)res & ~S.kill_w[lane] & S.valid_w[lane];
+        S.k_w[lane] = K;
+        const uint32_t pc = __popc(K);
+        if (P.stats) st_pos += pc;
+        // output: bits of positions p0 + 32*lane + b
+        if (K && P.bits) {
+          const uint64_t gpos = p0 + 32ull * lane;
+          const uint32_t sh = (uint32_t)(gpos & 31u);
+          const uint64_t gword = gpos >> 5;
+          if (sh == 0) {
+            atomicOr(&P.bits[gword], K);
+          } else {
+            const uint32_t a = K << sh, b = K >> (32u - sh);
+            if (a) atomicOr(&P.bits[gword], a);
+            if (b) atomicOr(&P.bits[gword + 1], b);
+          }
+        }
+      }
+      // prefix popcounts of the answer words (for per-read hit counts)
+      if (P.hits) {
+        __syncwarp();
+        uint32_t pc = lane < 16 ? __popc(S.k_w[lane]) : 0u;
+        uint32_t incl = pc;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          uint32_t a = __shfl_up_sync(kFull, incl, d);
+          if (lane >= d) incl += a;
+        }
+        if (lane < 16) S.pref_w[lane] = incl - pc;
+        if (lane == 16) {
+          S.pref_w[16] = incl;  // lane 16 holds the total (pc = 0 there)
+          S.k_w[16] = 0;
+        }
+        __syncwarp();
+        auto bits_before = [&](uint32_t x) -> uint32_t {  // x in [0, 512]
+          const uint32_t w = x >> 5, b = x & 31u;
+          return S.pref_w[w] + (b ? __popc(S.k_w[w] & (0xFFFFFFFFu >> (32u - b))) : 0u);
+        };
+        const uint64_t own_hi = p0 + ADV;
+        uint64_t q0 = r_cur;
+        while (true) {
+          const uint64_t q = q0 + lane;
+          uint64_t rs = ~0ull, re = ~0ull;
+          if (q < n_reads) {
+            rs = off[q];
+            re = off[q + 1];
+          }
+          if (q < n_reads && rs < own_hi && re > p0) {
+            const uint64_t a = rs > p0 ? rs - p0 : 0;
+            const uint64_t b = (re < own_hi ? re : own_hi) - p0;
+            if (b > a) {
+              const uint32_t cnt = bits_before((uint32_t)b) - bits_before((uint32_t)a);
+              if (cnt) atomicAdd(&P.hits[q], cnt);
+            }
+          }
+          const unsigned more = __ballot_sync(kFull, re < own_hi);
+          if (more != kFull) break;
+          q0 += 32;
+        }
+      }
+    }
+    r_cur += adv;
+    if (n_reads > 0 && r_cur > n_reads - 1) r_cur = n_reads - 1;
+    __syncwarp();
+  }
+
+  if (!INSERT && P.stats) {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+      st_valid += __shfl_down_sync(kFull, st_valid, d);
+      st_runs += __shfl_down_sync(kFull, st_runs, d);
+      st_pos += __shfl_down_sync(kFull, st_pos, d);
+    }
+    if (lane == 0) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(&P.stats[0]), st_valid);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&P.stats[1]), st_runs);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&P.stats[2]), st_pos);
+    }
+  }
+}
+
+template <int W, int H, int B, bool KEY64, bool INSERT>
+cudaError_t launch(const Params& P, cudaStream_t st) {
+  auto kern = fused_kernel<W, H, B, KEY64, INSERT>;
+  constexpr size_t smem = sizeof(WarpSmem<H, B>) * kWarps;
+  static int blocks_per_sm = 0;  // per instantiation; same on every GB300
+  if (blocks_per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    blocks_per_sm = nb > 0 ? nb : 1;
+  }
+  if (P.iters == 0) return cudaSuccess;
+  uint64_t want_blocks = (P.iters + kWarps - 1) / kWarps;
+  uint64_t cap = (uint64_t)sm_count() * blocks_per_sm;
+  int grid = (int)(want_blocks < cap ? want_blocks : cap);
+  if (grid < 1) grid = 1;
+  kern<<<grid, kThreads, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace fused
+}  // namespace sbf

@@ -1,0 +1,33 @@
+// sbf_fused_w12.cu -- fused kernels for minimizer window w = k - m + 1 = 12.
+#include "sbf_fused.cuh"
+
+namespace sbf {
+namespace fused {
+
+template <bool INSERT>
+static cudaError_t run(const Params& P, int H, int B, cudaStream_t st) {
+#ifdef SBF_MINIMAL_GRID
+  if (H == 4 && B == 512) return launch<12, 4, 512, true, INSERT>(P, st);
+  if (H == 4 && B == 256) return launch<12, 4, 256, true, INSERT>(P, st);
+#else
+  switch (H * 1000 + B) {
+    case 1256: return launch<12, 1, 256, true, INSERT>(P, st);
+    case 1512: return launch<12, 1, 512, true, INSERT>(P, st);
+    case 2256: return launch<12, 2, 256, true, INSERT>(P, st);
+    case 2512: return launch<12, 2, 512, true, INSERT>(P, st);
+    case 4256: return launch<12, 4, 256, true, INSERT>(P, st);
+    case 4512: return launch<12, 4, 512, true, INSERT>(P, st);
+    case 8256: return launch<12, 8, 256, true, INSERT>(P, st);
+    case 8512: return launch<12, 8, 512, true, INSERT>(P, st);
+    default: break;
+  }
+#endif
+  return cudaErrorNotSupported;
+}
+
+cudaError_t run_w12(const Params& P, int H, int B, bool insert, cudaStream_t st) {
+  return insert ? run<true>(P, H, B, st) : run<false>(P, H, B, st);
+}
+
+}  // namespace fused
+}  // namespace sbf

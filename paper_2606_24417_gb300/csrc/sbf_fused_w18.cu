@@ -1,0 +1,33 @@
+// sbf_fused_w18.cu -- fused kernels for minimizer window w = k - m + 1 = 18.
+#include "sbf_fused.cuh"
+
+namespace sbf {
+namespace fused {
+
+template <bool INSERT>
+static cudaError_t run(const Params& P, int H, int B, cudaStream_t st) {
+#ifdef SBF_MINIMAL_GRID
+  if (H == 4 && B == 512) return launch<18, 4, 512, false, INSERT>(P, st);
+  if (H == 4 && B == 256) return launch<18, 4, 256, false, INSERT>(P, st);
+#else
+  switch (H * 1000 + B) {
+    case 1256: return launch<18, 1, 256, false, INSERT>(P, st);
+    case 1512: return launch<18, 1, 512, false, INSERT>(P, st);
+    case 2256: return launch<18, 2, 256, false, INSERT>(P, st);
+    case 2512: return launch<18, 2, 512, false, INSERT>(P, st);
+    case 4256: return launch<18, 4, 256, false, INSERT>(P, st);
+    case 4512: return launch<18, 4, 512, false, INSERT>(P, st);
+    case 8256: return launch<18, 8, 256, false, INSERT>(P, st);
+    case 8512: return launch<18, 8, 512, false, INSERT>(P, st);
+    default: break;
+  }
+#endif
+  return cudaErrorNotSupported;
+}
+
+cudaError_t run_w18(const Params& P, int H, int B, bool insert, cudaStream_t st) {
+  return insert ? run<true>(P, H, B, st) : run<false>(P, H, B, st);
+}
+
+}  // namespace fused
+}  // namespace sbf

@@ -52,6 +52,7 @@ def load_library() -> ctypes.CDLL:
             "sbf_info": (I, [P] + [ctypes.POINTER(I)] * 6 + [ctypes.POINTER(U64)]),
             "sbf_num_words": (U64, [P]),
             "sbf_device_words": (P, [P]),
+            "sbf_kernel_variant": (I, [P]),
             "sbf_clear": (I, [P, P]),
             "sbf_get_bits": (I, [P, P]),
             "sbf_set_bits": (I, [P, P]),
@@ -145,6 +146,11 @@ class SuperBloomFilter:
     @property
     def nbytes(self) -> int:
         return self.n_words * 8
+
+    @property
+    def fused(self) -> bool:
+        """True if the fused kernels serve this filter (else the generic ones)."""
+        return bool(self._lib.sbf_kernel_variant(self._h))
 
     def device_words_ptr(self) -> int:
         return int(self._lib.sbf_device_words(self._h))

@@ -210,6 +210,58 @@ def test_checkpoint_roundtrip(tmp_path):
     assert torch.equal(qb1, qb2) and torch.equal(qh1, qh2)
 
 
+def test_fused_grid_is_used():
+    for params in [(31, 16, 28, 4, 512), (31, 12, 24, 8, 256), (31, 14, 26, 2, 512),
+                   (31, 20, 24, 1, 256)]:
+        k, m, s, H, B = params
+        assert make_filter(k, m, s, H, 1 << 20, B).fused, params
+    assert not make_filter(9, 5, 6, 2, 1 << 16, 256).fused
+
+
+@pytest.mark.parametrize("params", [(31, 16, 28, 4, 1 << 26, 512, True),
+                                    (31, 12, 24, 8, 1 << 25, 256, True),
+                                    (31, 20, 26, 2, 1 << 26, 512, False)],
+                         ids=lambda p: "_".join(map(str, p)))
+def test_fused_matches_generic_large(params, monkeypatch):
+    """Fused against generic kernels (a second, independent GPU path) on a
+    20 Mbp genome and 1M reads: identical words, bits and hits."""
+    k, m, s, H, bits, B, canon = params
+    g = synth.bacterial_genome(20_000_000, seed=8)
+    goff = np.array([0, g.size], dtype=np.uint64)
+    q, qoff = synth.mixed_query_reads(g, 500_000, 500_000, 150, 0.01, seed=9)
+    monkeypatch.setenv("SBF_FORCE_GENERIC", "1")
+    fg = make_filter(k, m, s, H, bits, B, canon)
+    monkeypatch.delenv("SBF_FORCE_GENERIC")
+    ff = make_filter(k, m, s, H, bits, B, canon)
+    assert ff.fused and not fg.fused
+    dg, dgo, dq, dqo = dev(g), dev_off(goff), dev(q), dev_off(qoff)
+    fg.insert(dg, dgo)
+    ff.insert(dg, dgo)
+    assert np.array_equal(fg.words(), ff.words())
+    sg = torch.zeros(3, dtype=torch.int64, device="cuda")
+    sf = torch.zeros(3, dtype=torch.int64, device="cuda")
+    bg, hg = fg.query(dq, dqo, stats=sg)
+    bf, hf = ff.query(dq, dqo, stats=sf)
+    assert torch.equal(bg, bf) and torch.equal(hg, hf) and torch.equal(sg, sf)
+
+
+def test_unaligned_sequence_pointer():
+    params = (31, 16, 28, 4, 1 << 22, 512, True)
+    seq, off = ragged_reads(2000, 51)
+    buf = torch.empty(seq.size + 3, dtype=torch.uint8, device="cuda")
+    buf[3:] = dev(seq)
+    dseq = buf[3:]
+    assert dseq.data_ptr() % 16 != 0
+    f = make_filter(*params[:5], params[5], params[6])
+    o = OracleSBF(*params[:5], shard_bits=params[5])
+    f.insert(dseq, dev_off(off))
+    o.insert(seq, off)
+    assert np.array_equal(f.words(), o.words())
+    qb, qh = f.query(dseq, dev_off(off))
+    ob, oh = o.query(seq, off)
+    assert np.array_equal(u32(qb), ob) and np.array_equal(u32(qh), oh)
+
+
 # ---------------------------------------------------------------------------
 # bacterial-genome workload at full size: 100 Mbp Markov genome with repeats,
 # 2^30-bit filter, 10M sampled reads (1% errors) + 10M random 150 bp reads
