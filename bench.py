@@ -108,12 +108,13 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
-def make_workload(rank: int):
+def make_workload(rank: int, small: bool = False):
     from paper_2606_24417_gb300 import synth
 
     t = time.time()
     genome = synth.bacterial_genome(GENOME_BP, seed=2)
-    reads, roff = synth.mixed_query_reads(genome, N_SAMPLED, N_RANDOM, READ_LEN, 0.01,
+    n_s, n_r = (N_SAMPLED // 10, N_RANDOM // 10) if small else (N_SAMPLED, N_RANDOM)
+    reads, roff = synth.mixed_query_reads(genome, n_s, n_r, READ_LEN, 0.01,
                                           seed=3 + 1000 * rank)
     log(f"[bench] rank {rank}: workload generated in {time.time() - t:.1f}s")
     return genome, reads, roff
@@ -239,7 +240,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
 
-    genome, reads, roff = make_workload(rank)
+    genome, reads, roff = make_workload(rank, small=args.case == "small")
     n_reads = roff.size - 1
     goff = np.array([0, genome.size], dtype=np.uint64)
     ins_kmers = genome.size - K + 1
@@ -306,6 +307,12 @@ def run_ours(args, rank, world, local_rank):
     else:
         ins_ms_sum, q_ms_sum = sum(t_ins), sum(t_q)
     value = world * kmers_step * args.steps / (total_ms / 1e3)
+
+    if args.skip_extras:
+        if rank == 0:
+            print(json.dumps({"case": args.case, "query_ms": sum(t_q) / args.steps,
+                              "insert_ms": sum(t_ins) / args.steps, "value": value}), flush=True)
+        return 0
 
     # ---- e2e through the host entry points (pinned host buffers) ----------
     h_genome = torch.from_numpy(genome).pin_memory().numpy()
@@ -391,6 +398,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--case", default="full", choices=["full", "small"],
+                    help="small: 2M query reads (300 MB, still larger than L2) for profiling")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="device-timed steps only (no e2e, no CPU baseline): profiling runs")
     args = ap.parse_args()
     if args.warmup < 3:
         log("[bench] warmup raised to 3")

@@ -42,7 +42,7 @@ namespace fused {
 constexpr int kLanePos = 16;        // start positions per lane
 constexpr int kWarps = 4;           // warps per block
 constexpr int kThreads = 32 * kWarps;
-constexpr int kSlotCap = 96;        // runs per iteration with a shard copy in shared memory
+constexpr int kSlotCap = 64;        // runs per iteration with a shard copy in shared memory
 constexpr int kStage = 34;          // staged 16-base words per iteration (544 bases)
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
@@ -80,6 +80,9 @@ struct Layout {
   static constexpr int q = 64 / H;                   // slice width (>= b for H <= 8)
   static constexpr int W32 = B / 32;                 // 32-bit words per shard
   static constexpr int SW32 = SB / 32;               // 32-bit words per sector
+  // slot stride in shared memory: W32 + 4 words keeps 16-byte alignment for
+  // cp.async and spreads consecutive slots over different banks
+  static constexpr int SLOT = W32 + 4;
   using Pack = typename std::conditional<(H == 8), uint64_t, uint32_t>::type;
   static_assert(q >= b, "bit-slicing only");
 };
@@ -123,15 +126,18 @@ struct Params {
   uint64_t iters;     // total iterations over the sequence
 };
 
-template <int H, int B>
+template <int H, int B, bool KEY64>
 struct alignas(16) WarpSmem {
   using L = Layout<H, B>;
   using Pack = typename L::Pack;
+  // minimizer key, then shard index, per slot (32-bit unless the key is 64-bit;
+  // the 32-bit form needs fewer than 2^32 shards)
+  using SlotT = typename std::conditional<KEY64, uint64_t, uint32_t>::type;
   static constexpr int kHsStride = sizeof(Pack) == 4 ? 34 : 33;  // bank-conflict-free transposes
-  uint32_t shard[kSlotCap * L::W32];     // shard copies (query) or masks (insert)
-  uint64_t slot_x[512];                  // minimizer key, then shard index, per slot
+  uint32_t shard[kSlotCap * L::SLOT];    // shard copies (query) or masks (insert)
+  SlotT slot_x[512];
   Pack hs[kLanePos * kHsStride];         // s-mer bit-address packs, [j][lane]
-  uint16_t slot_of[512];                 // slot of each valid position
+  uint16_t slot_of[kLanePos * 34];       // slot of each valid position, [j][lane]
   uint16_t end_list[512];                // run-end positions
   uint16_t slot_head[512];               // run-head position of each slot
   uint32_t fwd[kStage];                  // staged 2-bit words
@@ -243,14 +249,15 @@ __device__ bool prev_kmer_key(const Geom& g, const uint8_t* seq, uint64_t seq_le
 }
 
 template <int W, int H, int B, bool KEY64, bool INSERT>
-__global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
+__global__ void __launch_bounds__(kThreads, 4) fused_kernel(Params P) {
   using L = Layout<H, B>;
   using Pack = typename L::Pack;
   using KeyT = typename std::conditional<KEY64, uint64_t, uint32_t>::type;
-  using Sm = WarpSmem<H, B>;
+  using Sm = WarpSmem<H, B, KEY64>;
   constexpr int U = Shape<W>::kUseful;
   constexpr int ADV = Shape<W>::kAdvance;
   constexpr int HS = Sm::kHsStride;
+  constexpr int SO = 34;  // slot_of stride ([j][lane] layout)
 
   extern __shared__ __align__(16) uint8_t smem_raw[];
   Sm& S = reinterpret_cast<Sm*>(smem_raw)[threadIdx.x >> 5];
@@ -281,8 +288,22 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
   const uint64_t mmask = (m >= 32) ? ~0ull : ((1ull << (2 * m)) - 1ull);
   uint32_t* words32 = reinterpret_cast<uint32_t*>(g.words);
 
+  // end of read q (clamped), or "infinity" past the last read
+  auto read_end = [&](uint64_t q) -> uint64_t {
+    if (q >= n_reads) return ~0ull;
+    uint64_t e = off[q + 1];
+    return e < seq_len ? e : seq_len;
+  };
+
   uint64_t p0 = it0 * (uint64_t)ADV;
   uint64_t r_cur = n_reads > 0 ? warp_find_read(off, n_reads, p0, lane) : 0;
+  uint64_t r_cur_start = 0;                              // start of read r_cur (clamped)
+  if (n_reads > 0) r_cur_start = off[r_cur] < seq_len ? off[r_cur] : seq_len;
+  uint64_t e_batch = read_end(r_cur + lane);              // prefetched first batch of read ends
+  // prefetched raw bytes of the first iteration
+  uint4 raw_a = load16(P.seq, p0 + 16ull * lane, seq_len, aligned);
+  uint4 raw_b = make_uint4(0, 0, 0, 0);
+  if (lane < kStage - 32) raw_b = load16(P.seq, p0 + 16ull * (lane + 32), seq_len, aligned);
 
   // run-head carry: validity and minimizer key of position p0 - 1
   bool carry_valid = false;
@@ -303,23 +324,32 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
 
   for (uint64_t it = it0; it < it1; ++it, p0 += ADV) {
     // ---------------- staging: encode 544 bases once ----------------------
-    for (int wi = lane; wi < kStage; wi += 32) {
-      uint64_t pos = p0 + 16ull * wi;
-      uint4 raw = load16(P.seq, pos, seq_len, aligned);
-      uint32_t c8, b4, fw = 0, bad = 0;
-      encode4(raw.x, c8, b4); fw = c8;             bad = b4;
-      encode4(raw.y, c8, b4); fw = (fw << 8) | c8; bad |= b4 << 4;
-      encode4(raw.z, c8, b4); fw = (fw << 8) | c8; bad |= b4 << 8;
-      encode4(raw.w, c8, b4); fw = (fw << 8) | c8; bad |= b4 << 12;
-      if (pos < lo_pos || pos + 16 > hi_pos) {  // outside the reads' span
-        uint32_t okm = 0;
+    {
+      auto stage = [&](int wi, const uint4& raw) {
+        const uint64_t pos = p0 + 16ull * wi;
+        uint32_t c8, b4, fw, bad;
+        encode4(raw.x, c8, b4); fw = c8;             bad = b4;
+        encode4(raw.y, c8, b4); fw = (fw << 8) | c8; bad |= b4 << 4;
+        encode4(raw.z, c8, b4); fw = (fw << 8) | c8; bad |= b4 << 8;
+        encode4(raw.w, c8, b4); fw = (fw << 8) | c8; bad |= b4 << 12;
+        if (pos < lo_pos || pos + 16 > hi_pos) {  // outside the reads' span
+          uint32_t okm = 0;
 #pragma unroll
-        for (int b = 0; b < 16; ++b) okm |= (uint32_t)(pos + b >= lo_pos && pos + b < hi_pos) << b;
-        bad |= ~okm & 0xFFFFu;
+          for (int b = 0; b < 16; ++b) okm |= (uint32_t)(pos + b >= lo_pos && pos + b < hi_pos) << b;
+          bad |= ~okm & 0xFFFFu;
+        }
+        S.fwd[wi] = fw;
+        S.rcw[wi] = ~pairswap(__brev(fw));
+        S.bad[wi] = bad;
+      };
+      stage(lane, raw_a);
+      if (lane < kStage - 32) stage(lane + 32, raw_b);
+      // prefetch the next iteration's bytes; they arrive while this one runs
+      if (it + 1 < it1) {
+        const uint64_t np = p0 + ADV;
+        raw_a = load16(P.seq, np + 16ull * lane, seq_len, aligned);
+        if (lane < kStage - 32) raw_b = load16(P.seq, np + 16ull * (lane + 32), seq_len, aligned);
       }
-      S.fwd[wi] = fw;
-      S.rcw[wi] = ~pairswap(__brev(fw));
-      S.bad[wi] = bad;
     }
     if (lane < 17) {
       S.kill_w[lane] = 0;
@@ -336,16 +366,12 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
     // ---------------- read ends inside the window; cursor advance --------
     uint64_t E48 = 0;
     uint64_t adv = 0;
+    const uint64_t own_hi = p0 + ADV;
     {
-      const uint64_t win_hi = p0 + 16ull * kStage, own_hi = p0 + ADV;
+      const uint64_t win_hi = p0 + 16ull * kStage;
       uint64_t q0 = r_cur;
+      uint64_t e = e_batch;
       while (true) {
-        uint64_t q = q0 + lane;
-        uint64_t e = ~0ull;
-        if (q < n_reads) {
-          e = off[q + 1];
-          if (e > seq_len) e = seq_len;
-        }
         unsigned bw = __ballot_sync(kFull, e < win_hi);
         adv += __popc(__ballot_sync(kFull, e <= own_hi));
         unsigned bb = bw;
@@ -358,6 +384,7 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
         }
         if (bw != kFull) break;
         q0 += 32;
+        e = read_end(q0 + lane);
       }
     }
 
@@ -376,23 +403,17 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
       if (lane >= U) valid16 = 0;
     }
 
-    // ---------------- per position: s-mer packs and m-mer keys ------------
+    // ---------------- m-mer order keys --------------------------------------
     KeyT key[kLanePos];
 #pragma unroll
     for (int j = 0; j < kLanePos; ++j) {
       const uint32_t hi = __funnelshift_l(F1, F0, 2 * j);
-      const uint32_t lo = __funnelshift_l(F2, F1, 2 * j);
       const uint32_t rlo = __funnelshift_r(R2, R1, 2 * j);
-      const uint32_t rhi = __funnelshift_r(R1, R0, 2 * j);
-      const uint64_t x64 = ((uint64_t)hi << 32) | lo;
-      const uint64_t r64 = ((uint64_t)rhi << 32) | rlo;
-      uint64_t fs = x64 >> (64 - 2 * s);
-      uint64_t rs = r64 & smask;
-      uint64_t cs = (canon && rs < fs) ? rs : fs;
-      S.hs[j * HS + lane] = make_pack<H, B>(mix64(cs ^ kSmerKey));
       if constexpr (KEY64) {
-        uint64_t fm = x64 >> (64 - 2 * m);
-        uint64_t rm = r64 & mmask;
+        const uint32_t lo = __funnelshift_l(F2, F1, 2 * j);
+        const uint32_t rhi = __funnelshift_r(R1, R0, 2 * j);
+        uint64_t fm = (((uint64_t)hi << 32) | lo) >> (64 - 2 * m);
+        uint64_t rm = (((uint64_t)rhi << 32) | rlo) & mmask;
         uint64_t cm = (canon && rm < fm) ? rm : fm;
         key[j] = cm * kGolden64;
       } else {
@@ -405,34 +426,27 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
 
     // ---------------- sliding minimum over W windows (van Herk) -----------
     constexpr int NE = 15 + W;  // positions 0 .. 15+W-1 of the extended chunk
-    KeyT ext[NE];
-#pragma unroll
-    for (int i = 0; i < NE; ++i) {
-      if (i < 16) {
-        ext[i] = key[i];
-      } else if (i < 32) {
-        if constexpr (KEY64) {
-          uint32_t h = __shfl_down_sync(kFull, (uint32_t)(key[i - 16] >> 32), 1);
-          uint32_t l = __shfl_down_sync(kFull, (uint32_t)key[i - 16], 1);
-          ext[i] = ((uint64_t)h << 32) | l;
-        } else {
-          ext[i] = __shfl_down_sync(kFull, key[i - 16], 1);
-        }
-      } else {
-        if constexpr (KEY64) {
-          uint32_t h = __shfl_down_sync(kFull, (uint32_t)(key[i - 32] >> 32), 2);
-          uint32_t l = __shfl_down_sync(kFull, (uint32_t)key[i - 32], 2);
-          ext[i] = ((uint64_t)h << 32) | l;
-        } else {
-          ext[i] = __shfl_down_sync(kFull, key[i - 32], 2);
-        }
-      }
-    }
     KeyT mk[kLanePos];
     {
-      // blocks [0, W), [W, 2W), ...: suffix minima inside each block and
-      // prefix minima inside each block; window [j, j+W-1] = suffix(j) and
-      // prefix(j+W-1) of the next block.
+      KeyT ext[NE];
+#pragma unroll
+      for (int i = 0; i < NE; ++i) {
+        if (i < 16) {
+          ext[i] = key[i];
+        } else {
+          const int src = i < 32 ? i - 16 : i - 32;
+          const int dl = i < 32 ? 1 : 2;
+          if constexpr (KEY64) {
+            uint32_t h = __shfl_down_sync(kFull, (uint32_t)(key[src] >> 32), dl);
+            uint32_t l = __shfl_down_sync(kFull, (uint32_t)key[src], dl);
+            ext[i] = ((uint64_t)h << 32) | l;
+          } else {
+            ext[i] = __shfl_down_sync(kFull, key[src], dl);
+          }
+        }
+      }
+      // blocks [0, W), [W, 2W), ...: window [j, j+W-1] = suffix minimum of
+      // j's block from j, and prefix minimum of the next block up to j+W-1.
       KeyT suf[NE], pre[NE];
 #pragma unroll
       for (int i = NE - 1; i >= 0; --i) {
@@ -530,10 +544,10 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
         const uint32_t t = 16u * lane + j;
         if ((slot16 >> j) & 1u) {
           ++sl;
-          S.slot_x[sl] = (uint64_t)mk[j];
+          S.slot_x[sl] = (typename Sm::SlotT)mk[j];
           S.slot_head[sl] = (uint16_t)t;
         }
-        if ((valid16 >> j) & 1u) S.slot_of[t] = (uint16_t)sl;
+        if ((valid16 >> j) & 1u) S.slot_of[j * SO + lane] = (uint16_t)sl;
         if ((end16 >> j) & 1u) S.end_list[en++] = (uint16_t)t;
       }
     }
@@ -543,9 +557,12 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
       S.valid_w[16] = 0;
       S.end_w[16] = 0;
     }
+    // prefetch the first batch of read ends of the next iteration
+    const uint64_t r_next = (n_reads > 0 && r_cur + adv > n_reads - 1) ? n_reads - 1 : r_cur + adv;
+    const uint64_t e_next = read_end(r_next + lane);
     __syncwarp();
 
-    // ---------------- shards of the runs ----------------------------------
+    // ---------------- shards of the runs: index, then async copy ----------
     const uint64_t n_shards = g.n_shards;
     for (uint32_t si = lane; si < total_slots; si += 32) {
       uint64_t mu;
@@ -555,15 +572,15 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
         mu = (uint32_t)S.slot_x[si] * inv32(kGolden32);
       }
       uint64_t x = __umul64hi(mix64(mu ^ kShardKey), n_shards);
-      S.slot_x[si] = x;
+      S.slot_x[si] = (typename Sm::SlotT)x;
       if (si < (uint32_t)kSlotCap) {
         if constexpr (INSERT) {
 #pragma unroll
           for (int w = 0; w < L::W32; w += 4)
-            *reinterpret_cast<uint4*>(&S.shard[si * L::W32 + w]) = make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint4*>(&S.shard[si * L::SLOT + w]) = make_uint4(0, 0, 0, 0);
         } else {
           const uint8_t* src = reinterpret_cast<const uint8_t*>(g.words) + x * (uint64_t)(B / 8);
-          uint32_t dst = (uint32_t)__cvta_generic_to_shared(&S.shard[si * L::W32]);
+          uint32_t dst = (uint32_t)__cvta_generic_to_shared(&S.shard[si * L::SLOT]);
 #pragma unroll
           for (int c = 0; c < B / 128; ++c)
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16 * c),
@@ -571,86 +588,119 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
         }
       }
     }
-    if constexpr (!INSERT) {
-      asm volatile("cp.async.commit_group;\n" ::);
-      asm volatile("cp.async.wait_group 0;\n" ::);
+    if constexpr (!INSERT) asm volatile("cp.async.commit_group;\n" ::);
+
+    // ---------------- s-mer bit-address packs (overlaps the copies) -------
+#pragma unroll
+    for (int j = 0; j < kLanePos; ++j) {
+      const uint32_t hi = __funnelshift_l(F1, F0, 2 * j);
+      const uint32_t lo = __funnelshift_l(F2, F1, 2 * j);
+      const uint32_t rlo = __funnelshift_r(R2, R1, 2 * j);
+      const uint32_t rhi = __funnelshift_r(R1, R0, 2 * j);
+      const uint64_t fs = (((uint64_t)hi << 32) | lo) >> (64 - 2 * s);
+      const uint64_t rs = (((uint64_t)rhi << 32) | rlo) & smask;
+      const uint64_t cs = (canon && rs < fs) ? rs : fs;
+      S.hs[j * HS + lane] = make_pack<H, B>(mix64(cs ^ kSmerKey));
     }
+    if constexpr (!INSERT) asm volatile("cp.async.wait_group 0;\n" ::);
     __syncwarp();
 
-    // ---------------- own pairs: (t, shard(t)) ----------------------------
-    auto word_of = [&](uint32_t slot, uint32_t widx) -> uint32_t {
-      if (slot < (uint32_t)kSlotCap) return S.shard[slot * L::W32 + widx];
-      return __ldg(words32 + S.slot_x[slot] * (uint64_t)L::W32 + widx);
-    };
+    // ---------------- pair tests / sets ------------------------------------
     auto test_pair = [&](Pack pk, uint32_t slot) -> bool {
       uint32_t acc = 1u;
+      if (slot < (uint32_t)kSlotCap) {
+        const uint32_t* sp = &S.shard[slot * L::SLOT];
 #pragma unroll
-      for (int i = 0; i < H; ++i) {
-        const uint32_t p = pack_addr<H, B>(pk, i);
-        const uint32_t widx = (uint32_t)(i % L::S) * L::SW32 + (p >> 5);
-        const uint32_t w = word_of(slot, widx);
-        acc &= __funnelshift_r(w, w, p);
+        for (int i = 0; i < H; ++i) {
+          const uint32_t p = pack_addr<H, B>(pk, i);
+          const uint32_t w = sp[(i % L::S) * L::SW32 + (p >> 5)];
+          acc &= __funnelshift_r(w, w, p);
+        }
+      } else {
+        const uint32_t* gp = words32 + S.slot_x[slot] * (uint64_t)L::W32;
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+          const uint32_t p = pack_addr<H, B>(pk, i);
+          const uint32_t w = __ldg(gp + (i % L::S) * L::SW32 + (p >> 5));
+          acc &= __funnelshift_r(w, w, p);
+        }
       }
       return acc & 1u;
     };
     auto set_pair = [&](Pack pk, uint32_t slot) {
+      if (slot < (uint32_t)kSlotCap) {
+        uint32_t* sp = &S.shard[slot * L::SLOT];
 #pragma unroll
-      for (int i = 0; i < H; ++i) {
-        const uint32_t p = pack_addr<H, B>(pk, i);
-        const uint32_t widx = (uint32_t)(i % L::S) * L::SW32 + (p >> 5);
-        const uint32_t bit = 1u << (p & 31u);
-        if (slot < (uint32_t)kSlotCap) {
-          atomicOr(&S.shard[slot * L::W32 + widx], bit);
-        } else {
-          atomicOr(&words32[S.slot_x[slot] * (uint64_t)L::W32 + widx], bit);
+        for (int i = 0; i < H; ++i) {
+          const uint32_t p = pack_addr<H, B>(pk, i);
+          atomicOr(&sp[(i % L::S) * L::SW32 + (p >> 5)], 1u << (p & 31u));
+        }
+      } else {
+        uint32_t* gp = words32 + S.slot_x[slot] * (uint64_t)L::W32;
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+          const uint32_t p = pack_addr<H, B>(pk, i);
+          atomicOr(&gp[(i % L::S) * L::SW32 + (p >> 5)], 1u << (p & 31u));
         }
       }
     };
 
+    // own pairs (t, shard(t)), position-per-lane: t = 32*pass + lane, so
+    // t & 15 = lane & 15 and t >> 4 = 2*pass + (lane >> 4)
+    {
+      const uint32_t hs_i0 = (lane & 15u) * HS + (lane >> 4);
+      const uint32_t so_i0 = (lane & 15u) * SO + (lane >> 4);
 #pragma unroll 1
-    for (int pass = 0; pass < 16; ++pass) {
-      const uint32_t t = 32u * pass + lane;
-      const bool v = (S.valid_w[pass] >> lane) & 1u;
-      bool ok = false;
-      if (v) {
-        const Pack pk = S.hs[(t & 15u) * HS + (t >> 4)];
-        const uint32_t slot = S.slot_of[t];
-        if constexpr (INSERT) {
-          set_pair(pk, slot);
-        } else {
-          ok = test_pair(pk, slot);
+      for (int pass = 0; pass < 16; ++pass) {
+        const bool v = (S.valid_w[pass] >> lane) & 1u;
+        bool ok = false;
+        if (v) {
+          const Pack pk = S.hs[hs_i0 + 2 * pass];
+          const uint32_t slot = S.slot_of[so_i0 + 2 * pass];
+          if constexpr (INSERT) {
+            set_pair(pk, slot);
+          } else {
+            ok = test_pair(pk, slot);
+          }
         }
-      }
-      if constexpr (!INSERT) {
-        const unsigned own = __ballot_sync(kFull, ok);
-        if (lane == 0) S.own_w[pass] = own;
+        if constexpr (!INSERT) {
+          const unsigned own = __ballot_sync(kFull, ok);
+          if (lane == 0) S.own_w[pass] = own;
+        }
       }
     }
 
-    // ---------------- extra pairs after each run end: (e+d, shard(e)) ----
-#pragma unroll 1
-    for (int d = 1; d <= z; ++d) {
-      for (uint32_t ei = lane; ei < total_ends; ei += 32) {
-        const uint32_t e = S.end_list[ei];
-        const uint32_t t = e + d;
-        const uint32_t slot = S.slot_of[e];
-        const Pack pk = S.hs[(t & 15u) * HS + (t >> 4)];
-        if constexpr (INSERT) {
-          set_pair(pk, slot);
-        } else {
-          if (!test_pair(pk, slot)) {
-            // k-mers [max(t - z, run head), e] of this run need s-mer t
-            int lo = (int)t - z;
-            const int hd = S.slot_head[slot];
-            if (lo < hd) lo = hd;
-            const uint32_t w1 = (uint32_t)lo >> 5, w2 = e >> 5;
-            const uint32_t bl = (uint32_t)lo & 31u, bh = e & 31u;
-            if (w1 == w2) {
-              atomicOr(&S.kill_w[w1], (0xFFFFFFFFu >> (31u - bh)) & (0xFFFFFFFFu << bl));
-            } else {
-              atomicOr(&S.kill_w[w1], 0xFFFFFFFFu << bl);
-              atomicOr(&S.kill_w[w2], 0xFFFFFFFFu >> (31u - bh));
-            }
+    // extra pairs after each run end e: (e+d, shard(e)), d = 1..z.  A failure
+    // at d kills the run's k-mers [max(e+d-z, head), e]; the smallest failing
+    // d gives the largest range, so testing stops there.
+    for (uint32_t ei = lane; ei < total_ends; ei += 32) {
+      const uint32_t e = S.end_list[ei];
+      const uint32_t slot = S.slot_of[(e & 15u) * SO + (e >> 4)];
+      if constexpr (INSERT) {
+        for (int d = 1; d <= z; ++d) {
+          const uint32_t t = e + d;
+          set_pair(S.hs[(t & 15u) * HS + (t >> 4)], slot);
+        }
+      } else {
+        int fail = 0;
+        for (int d = 1; d <= z; ++d) {
+          const uint32_t t = e + d;
+          if (!test_pair(S.hs[(t & 15u) * HS + (t >> 4)], slot)) {
+            fail = d;
+            break;
+          }
+        }
+        if (fail) {
+          int lo = (int)e + fail - z;
+          const int hd = S.slot_head[slot];
+          if (lo < hd) lo = hd;
+          const uint32_t w1 = (uint32_t)lo >> 5, w2 = e >> 5;
+          const uint32_t bl = (uint32_t)lo & 31u, bh = e & 31u;
+          if (w1 == w2) {
+            atomicOr(&S.kill_w[w1], (0xFFFFFFFFu >> (31u - bh)) & (0xFFFFFFFFu << bl));
+          } else {
+            atomicOr(&S.kill_w[w1], 0xFFFFFFFFu << bl);
+            atomicOr(&S.kill_w[w2], 0xFFFFFFFFu >> (31u - bh));
           }
         }
       }
@@ -660,16 +710,15 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
     if constexpr (INSERT) {
       // ---------------- flush run masks: coalesced 64-bit atomics ----------
       const uint32_t n_mem = total_slots < (uint32_t)kSlotCap ? total_slots : (uint32_t)kSlotCap;
-      const uint32_t n_words = n_mem * (B / 64);
-      const uint64_t* sm64 = reinterpret_cast<const uint64_t*>(S.shard);
+      constexpr uint32_t W64 = B / 64;
+      const uint32_t n_words = n_mem * W64;
       for (uint32_t i = lane; i < n_words; i += 32) {
-        const uint32_t si = i / (B / 64), wd = i % (B / 64);
-        const uint64_t v = sm64[i];
+        const uint32_t si = i / W64, wd = i % W64;
+        const uint64_t v = *reinterpret_cast<const uint64_t*>(&S.shard[si * L::SLOT + 2 * wd]);
         if (v)
-          atomicOr(reinterpret_cast<unsigned long long*>(g.words) + S.slot_x[si] * (uint64_t)(B / 64) + wd,
+          atomicOr(reinterpret_cast<unsigned long long*>(g.words) + S.slot_x[si] * (uint64_t)W64 + wd,
                    (unsigned long long)v);
       }
-      __syncwarp();
     } else {
       // ---------------- Findere AND inside runs -> answer words -----------
       if (lane < 16) {
@@ -682,8 +731,7 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
         }
         const uint32_t K = (uint32_t)res & ~S.kill_w[lane] & S.valid_w[lane];
         S.k_w[lane] = K;
-        const uint32_t pc = __popc(K);
-        if (P.stats) st_pos += pc;
+        if (P.stats) st_pos += __popc(K);
         // output: bits of positions p0 + 32*lane + b
         if (K && P.bits) {
           const uint64_t gpos = p0 + 32ull * lane;
@@ -698,10 +746,10 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
           }
         }
       }
-      // prefix popcounts of the answer words (for per-read hit counts)
+      // per-read hit counts from prefix popcounts of the answer words
       if (P.hits) {
         __syncwarp();
-        uint32_t pc = lane < 16 ? __popc(S.k_w[lane]) : 0u;
+        const uint32_t pc = lane < 16 ? __popc(S.k_w[lane]) : 0u;
         uint32_t incl = pc;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -718,15 +766,14 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
           const uint32_t w = x >> 5, b = x & 31u;
           return S.pref_w[w] + (b ? __popc(S.k_w[w] & (0xFFFFFFFFu >> (32u - b))) : 0u);
         };
-        const uint64_t own_hi = p0 + ADV;
+        // batch 0 reuses the prefetched read ends: read q = r_cur + lane spans
+        // [end of q-1, end of q)
         uint64_t q0 = r_cur;
+        uint64_t re = e_batch;
+        uint64_t rs = __shfl_up_sync(kFull, re, 1);
+        if (lane == 0) rs = r_cur_start;
         while (true) {
           const uint64_t q = q0 + lane;
-          uint64_t rs = ~0ull, re = ~0ull;
-          if (q < n_reads) {
-            rs = off[q];
-            re = off[q + 1];
-          }
           if (q < n_reads && rs < own_hi && re > p0) {
             const uint64_t a = rs > p0 ? rs - p0 : 0;
             const uint64_t b = (re < own_hi ? re : own_hi) - p0;
@@ -737,12 +784,26 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
           }
           const unsigned more = __ballot_sync(kFull, re < own_hi);
           if (more != kFull) break;
+          const uint64_t last_end = __shfl_sync(kFull, re, 31);
           q0 += 32;
+          re = read_end(q0 + lane);
+          rs = __shfl_up_sync(kFull, re, 1);
+          if (lane == 0) rs = last_end;
         }
       }
     }
-    r_cur += adv;
-    if (n_reads > 0 && r_cur > n_reads - 1) r_cur = n_reads - 1;
+    // advance the read cursor (adv is warp-uniform): the new current read
+    // starts where read r_next - 1 ends
+    if (adv > 0) {
+      if (r_cur + adv > r_next || adv > 32) {
+        const uint64_t st = off[r_next];
+        r_cur_start = st < seq_len ? st : seq_len;
+      } else {
+        r_cur_start = __shfl_sync(kFull, e_batch, (int)(adv - 1));
+      }
+    }
+    r_cur = r_next;
+    e_batch = e_next;
     __syncwarp();
   }
 
@@ -764,7 +825,7 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(Params P) {
 template <int W, int H, int B, bool KEY64, bool INSERT>
 cudaError_t launch(const Params& P, cudaStream_t st) {
   auto kern = fused_kernel<W, H, B, KEY64, INSERT>;
-  constexpr size_t smem = sizeof(WarpSmem<H, B>) * kWarps;
+  constexpr size_t smem = sizeof(WarpSmem<H, B, KEY64>) * kWarps;
   static int blocks_per_sm = 0;  // per instantiation; same on every GB300
   if (blocks_per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

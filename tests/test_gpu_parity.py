@@ -158,6 +158,19 @@ def test_edge_cases():
     assert oh[0] == 0 and oh[1] == 1 and oh[2] == 0 and oh[3] == 0 and oh[4] == 1
 
 
+@pytest.mark.parametrize("params", [(31, 16, 28, 4, 1 << 22, 512, True),
+                                    (31, 20, 24, 4, 1 << 22, 256, True)],
+                         ids=lambda p: "_".join(map(str, p)))
+def test_many_short_reads(params):
+    """Reads of 0-40 bases: more than 32 read ends fall in one kernel window,
+    so the boundary loops take several batches; most reads hold no k-mer."""
+    lens = synth.randint(61, 1, 60000, 0, 41)
+    seq = synth.uniform_dna(int(lens.sum()), 62)
+    off = np.zeros(lens.size + 1, dtype=np.uint64)
+    np.cumsum(lens, out=off[1:])
+    check_insert_query(params, seq, off, seq, off)
+
+
 def test_insert_order_and_repeats_on_gpu():
     params = (31, 16, 28, 4, 1 << 21, 512, True)
     seq, off = ragged_reads(3000, 21)
