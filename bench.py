@@ -395,6 +395,74 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# batched workload: 256 filters, one persistent launch vs one launch per filter
+# ---------------------------------------------------------------------------
+def run_batched(args):
+    import torch
+
+    from paper_2606_24417_gb300 import build_lib, synth
+    from paper_2606_24417_gb300.sbf import (BATCH_FUSED, BATCH_GRAPH, BATCH_PER_FILTER,
+                                            FilterBatch, SuperBloomFilter, num_kmers)
+
+    build_lib.build()
+    torch.cuda.set_device(0)
+    t = time.time()
+    w = synth.batched_workload(n_filters=256, n_reads=5_000_000, seed=4)
+    log(f"[bench] batched workload generated in {time.time() - t:.1f}s: "
+        f"{w['gseq'].size / 1e9:.2f} Gbp genomes, {w['seq'].size / 1e9:.2f} Gbp reads")
+    filters = [SuperBloomFilter(K, M, S, H, b, shard_bits=SHARD_BITS) for b in w["bits"]]
+    batch = FilterBatch(filters)
+    dg, dgo = torch.from_numpy(w["gseq"]).cuda(), torch.from_numpy(w["goff"].astype(np.int64)).cuda()
+    dq, dqo = torch.from_numpy(w["seq"]).cuda(), torch.from_numpy(w["off"].astype(np.int64)).cuda()
+    bits = torch.empty((w["seq"].size + 31) // 32, dtype=torch.int32, device="cuda")
+    hits = torch.empty(w["off"].size - 1, dtype=torch.int32, device="cuda")
+    ins_kmers = num_kmers(w["goff"], K)
+    q_kmers = num_kmers(w["off"], K)
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    res = {}
+    for name, mode in [("per_filter", BATCH_PER_FILTER), ("graph", BATCH_GRAPH)]:
+        res[f"insert_ms_{name}"] = timed(
+            lambda: batch.insert(dg, dgo, w["goff"], w["ggroup"], mode=mode), args.steps)
+    tuned_ms = batch.tune(dq, dqo, w["off"], w["group"], bits=bits, hits=hits)
+    answers = {}
+    for name, mode in [("per_filter", BATCH_PER_FILTER), ("fused", BATCH_FUSED), ("graph", BATCH_GRAPH)]:
+        res[f"query_ms_{name}"] = timed(
+            lambda: batch.query(dq, dqo, w["off"], w["group"], bits=bits, hits=hits, mode=mode),
+            args.steps)
+        torch.cuda.synchronize()
+        answers[name] = (bits.clone(), hits.clone())
+    same = all(torch.equal(answers[n][0], answers["per_filter"][0]) and
+               torch.equal(answers[n][1], answers["per_filter"][1]) for n in answers)
+    dyn, chunk, grid = batch.schedule()
+    line = {"workload": "batched: 256 filters of 2^20-2^28 bits (log-uniform sizes) built from "
+                        "1-50 Mbp uniform genomes (log-uniform), 5M reads of lognormal lengths "
+                        "(median 150 bp, sigma 1.5, cap 100 kb), half sampled with 1% errors",
+            "insert_kmers": ins_kmers, "query_kmers": q_kmers,
+            **{k: v for k, v in res.items()},
+            "query_kmers_per_s_graph": q_kmers / (res["query_ms_graph"] / 1e3),
+            "query_kmers_per_s_per_filter": q_kmers / (res["query_ms_per_filter"] / 1e3),
+            "insert_kmers_per_s_graph": ins_kmers / (res["insert_ms_graph"] / 1e3),
+            "insert_kmers_per_s_per_filter": ins_kmers / (res["insert_ms_per_filter"] / 1e3),
+            "tuned_schedule": {"dynamic": dyn, "chunk": chunk, "grid_blocks": grid,
+                               "tuned_query_ms": tuned_ms},
+            "answers_identical_across_modes": same}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -403,6 +471,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: 2M query reads (300 MB, still larger than L2) for profiling")
+    ap.add_argument("--workload", default="bacterial", choices=["bacterial", "batched"],
+                    help="batched: the many-filter workload (its own JSON line)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="device-timed steps only (no e2e, no CPU baseline): profiling runs")
     args = ap.parse_args()
@@ -414,6 +484,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batched":
+        return run_batched(args) if rank == 0 else 0
     if world > 1:
         import torch
         import torch.distributed as dist

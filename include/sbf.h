@@ -139,6 +139,53 @@ int sbf_query_seqs_host(const sbf_filter* f, const uint8_t* h_seq, uint64_t seq_
                         const uint64_t* h_off, uint64_t n_reads, uint32_t* h_kmer_bits,
                         uint32_t* h_read_hits);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many filters, one launch (scheduling only; the bits are those of
+ * the single-filter calls).  Not in the paper: its library serves one filter
+ * per call.
+ *
+ * A batch groups filters with equal (k, m, s, H, shard bits, canonical) and a
+ * fused kernel (sbf_kernel_variant = 1); sizes may differ.  The filters stay
+ * owned by the caller and must outlive the batch.  Reads are grouped by
+ * filter: filter f serves reads [h_group[f], h_group[f+1]) (h_group has
+ * n_filters + 1 entries, h_group[0] = 0, h_group[n_filters] = n_reads).
+ * Both the device offsets d_off and a host copy h_off are needed (the host
+ * copy sizes the per-filter work without a synchronisation).  Outputs are
+ * laid out as in sbf_query_seqs over the whole batch.
+ *
+ * mode: SBF_BATCH_PER_FILTER launches once per filter; SBF_BATCH_FUSED runs
+ * one persistent launch over a device table of all filters; SBF_BATCH_GRAPH
+ * captures that launch (with its memsets) into a CUDA graph on the first call
+ * and replays it while the arguments stay the same.  The batch owns a small
+ * device table and a work counter; calls on one batch must not overlap.
+ * ------------------------------------------------------------------------- */
+typedef struct sbf_batch sbf_batch;
+enum { SBF_BATCH_PER_FILTER = 0, SBF_BATCH_FUSED = 1, SBF_BATCH_GRAPH = 2 };
+
+int sbf_batch_create(sbf_filter* const* filters, int n_filters, sbf_batch** out);
+void sbf_batch_destroy(sbf_batch* b);
+int sbf_batch_insert(sbf_batch* b, const uint8_t* d_seq, uint64_t seq_len, const uint64_t* d_off,
+                     const uint64_t* h_off, uint64_t n_reads, const uint64_t* h_group, int mode,
+                     sbf_stream_t stream);
+int sbf_batch_query(sbf_batch* b, const uint8_t* d_seq, uint64_t seq_len, const uint64_t* d_off,
+                    const uint64_t* h_off, uint64_t n_reads, const uint64_t* h_group,
+                    uint32_t* d_kmer_bits, uint32_t* d_read_hits, int mode, sbf_stream_t stream);
+/* Schedule of the persistent launch: dynamic = 0 splits the iterations (496
+ * start positions each) into one contiguous share per warp; dynamic = 1 lets
+ * warps claim `chunk` iterations at a time from a device counter;
+ * grid_blocks caps the blocks (0 = full occupancy). */
+int sbf_batch_set_schedule(sbf_batch* b, int dynamic, uint32_t chunk, uint32_t grid_blocks);
+int sbf_batch_get_schedule(const sbf_batch* b, int* dynamic, uint32_t* chunk,
+                           uint32_t* grid_blocks);
+/* Autotuner: times every candidate schedule on this exact call (insert != 0:
+ * the insert) with CUDA events, keeps the fastest and returns its time in
+ * *best_ms.  Synchronises; the call's outputs are left as a normal call
+ * leaves them. */
+int sbf_batch_tune(sbf_batch* b, int insert, const uint8_t* d_seq, uint64_t seq_len,
+                   const uint64_t* d_off, const uint64_t* h_off, uint64_t n_reads,
+                   const uint64_t* h_group, uint32_t* d_kmer_bits, uint32_t* d_read_hits,
+                   sbf_stream_t stream, float* best_ms);
+
 /* Number of k-mer start positions sum_r max(0, len_r - k + 1) of a host
  * offset table (valid or not). */
 int sbf_num_kmers(const uint64_t* h_off, uint64_t n_reads, int k, uint64_t* out);

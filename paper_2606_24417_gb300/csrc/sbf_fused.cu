@@ -25,11 +25,32 @@ static cudaError_t run(const Params& P, bool insert, cudaStream_t st) {
   }
 }
 
-static uint64_t iterations(const Geom& g, uint64_t seq_len) {
+int advance_of(const Geom& g) {
   int w = window_of(g);
-  int adv = (15 + w - 1 >= 32 ? 30 : 31) * kLanePos;
-  return (seq_len + adv - 1) / adv;
+  return (15 + w - 1 >= 32 ? 30 : 31) * kLanePos;
 }
+
+// The single-segment launch of one call: positions [0, seq_len).
+static Params single(const Geom& g, const uint8_t* seq, uint64_t seq_len, const uint64_t* off,
+                     uint64_t n_reads, uint32_t* bits, uint32_t* hits, uint64_t* stats) {
+  Params P{};
+  P.g = g;
+  P.seq = seq;
+  P.seq_len = seq_len;
+  P.bits = bits;
+  P.stats = stats;
+  P.segs = nullptr;
+  P.n_segs = 1;
+  const uint64_t adv = (uint64_t)advance_of(g);
+  P.seg0 = Segment{g.words, g.n_shards, off, n_reads, hits, 0, 0, (seq_len + adv - 1) / adv};
+  P.iters = P.seg0.iters;
+  P.work = nullptr;
+  P.chunk = 1;
+  P.grid_blocks = 0;
+  return P;
+}
+
+cudaError_t launch_params(const Params& P, bool insert, cudaStream_t st) { return run(P, insert, st); }
 
 }  // namespace fused
 
@@ -51,8 +72,7 @@ bool fused_supported(const Geom& g) {
 cudaError_t fused_insert(const Geom& g, const uint8_t* seq, uint64_t seq_len, const uint64_t* off,
                          uint64_t n_reads, cudaStream_t st) {
   if (seq_len == 0 || n_reads == 0) return cudaSuccess;
-  fused::Params P{g, seq, seq_len, off, n_reads, nullptr, nullptr, nullptr,
-                  fused::iterations(g, seq_len)};
+  fused::Params P = fused::single(g, seq, seq_len, off, n_reads, nullptr, nullptr, nullptr);
   return fused::run(P, true, st);
 }
 
@@ -69,7 +89,7 @@ cudaError_t fused_query(const Geom& g, const uint8_t* seq, uint64_t seq_len, con
     if (e != cudaSuccess) return e;
   }
   if (seq_len == 0 || n_reads == 0) return cudaSuccess;
-  fused::Params P{g, seq, seq_len, off, n_reads, bits, hits, stats, fused::iterations(g, seq_len)};
+  fused::Params P = fused::single(g, seq, seq_len, off, n_reads, bits, hits, stats);
   return fused::run(P, false, st);
 }
 

@@ -114,16 +114,32 @@ __device__ __forceinline__ uint32_t pack_addr(typename Layout<H, B>::Pack pk, in
   }
 }
 
+// One filter's share of a launch: the filter, the reads it serves (a slice
+// of the offset table, absolute positions) and the positions to cover.
+struct Segment {
+  uint64_t* words;        // the filter's bit array
+  uint64_t n_shards;
+  const uint64_t* off;    // n_reads + 1 offsets (absolute positions in seq)
+  uint64_t n_reads;
+  uint32_t* hits;         // query: counts of these reads (zeroed by the launcher), or NULL
+  uint64_t p_begin;       // first position covered (multiple of 16)
+  uint64_t iter_begin;    // index of the segment's first iteration in the launch
+  uint64_t iters;         // iterations of kAdvance positions
+};
+
 struct Params {
-  Geom g;
+  Geom g;                 // shared k, m, s, H, shard bits, canonical
   const uint8_t* seq;
   uint64_t seq_len;
-  const uint64_t* off;
-  uint64_t n_reads;
-  uint32_t* bits;     // query: bit-packed answers (zeroed by the launcher)
-  uint32_t* hits;     // query: per-read counts (zeroed by the launcher)
-  uint64_t* stats;    // query: valid k-mers, runs, positives (may be NULL)
-  uint64_t iters;     // total iterations over the sequence
+  uint32_t* bits;         // query: bit-packed answers (zeroed by the launcher), or NULL
+  uint64_t* stats;        // query: valid k-mers, runs, positives, or NULL
+  const Segment* segs;    // NULL: the launch is the single segment seg0
+  uint32_t n_segs;
+  Segment seg0;
+  uint64_t iters;         // iterations over all segments
+  unsigned long long* work;  // dynamic scheduling counter (zeroed), or NULL for a static split
+  uint32_t chunk;         // iterations per dynamically claimed work item
+  uint32_t grid_blocks;   // blocks to launch (0: enough for the work, capped at full occupancy)
 };
 
 template <int H, int B, bool KEY64>
@@ -248,8 +264,13 @@ __device__ bool prev_kmer_key(const Geom& g, const uint8_t* seq, uint64_t seq_le
   return true;
 }
 
+// Iterations [it0, it1) of one segment, walked by one warp.
 template <int W, int H, int B, bool KEY64, bool INSERT>
-__global__ void __launch_bounds__(kThreads, 4) fused_kernel(Params P) {
+__device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params& P,
+                                          const Segment& seg, uint64_t it0, uint64_t it1,
+                                          int lane, unsigned long long& st_valid,
+                                          unsigned long long& st_runs,
+                                          unsigned long long& st_pos) {
   using L = Layout<H, B>;
   using Pack = typename L::Pack;
   using KeyT = typename std::conditional<KEY64, uint64_t, uint32_t>::type;
@@ -258,25 +279,15 @@ __global__ void __launch_bounds__(kThreads, 4) fused_kernel(Params P) {
   constexpr int ADV = Shape<W>::kAdvance;
   constexpr int HS = Sm::kHsStride;
   constexpr int SO = 34;  // slot_of stride ([j][lane] layout)
-
-  extern __shared__ __align__(16) uint8_t smem_raw[];
-  Sm& S = reinterpret_cast<Sm*>(smem_raw)[threadIdx.x >> 5];
-  const int lane = threadIdx.x & 31;
-  const Geom& g = P.g;
+  Geom g = P.g;
+  g.words = seg.words;
+  g.n_shards = seg.n_shards;
   const int k = g.k, m = g.m, s = g.s, z = g.k - g.s;
   const bool canon = g.canonical != 0;
 
-  // contiguous share of iterations for this warp
-  const uint64_t tw = (uint64_t)gridDim.x * kWarps;
-  const uint64_t gw = (uint64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-  const uint64_t per = P.iters / tw, rem = P.iters % tw;
-  const uint64_t it0 = gw * per + (gw < rem ? gw : rem);
-  const uint64_t it1 = it0 + per + (gw < rem ? 1 : 0);
-  if (it0 >= it1) return;
-
   const uint64_t seq_len = P.seq_len;
-  const uint64_t* off = P.off;
-  const uint64_t n_reads = P.n_reads;
+  const uint64_t* off = seg.off;
+  const uint64_t n_reads = seg.n_reads;
   // start positions outside [lo_pos, hi_pos) belong to no read
   uint64_t lo_pos = 0, hi_pos = 0;
   if (n_reads > 0) {
@@ -295,7 +306,7 @@ __global__ void __launch_bounds__(kThreads, 4) fused_kernel(Params P) {
     return e < seq_len ? e : seq_len;
   };
 
-  uint64_t p0 = it0 * (uint64_t)ADV;
+  uint64_t p0 = seg.p_begin + it0 * (uint64_t)ADV;
   uint64_t r_cur = n_reads > 0 ? warp_find_read(off, n_reads, p0, lane) : 0;
   uint64_t r_cur_start = 0;                              // start of read r_cur (clamped)
   if (n_reads > 0) r_cur_start = off[r_cur] < seq_len ? off[r_cur] : seq_len;
@@ -320,7 +331,6 @@ __global__ void __launch_bounds__(kThreads, 4) fused_kernel(Params P) {
       carry_key = __shfl_sync(kFull, kk, 0);
     }
   }
-  unsigned long long st_valid = 0, st_runs = 0, st_pos = 0;
 
   for (uint64_t it = it0; it < it1; ++it, p0 += ADV) {
     // ---------------- staging: encode 544 bases once ----------------------
@@ -747,7 +757,7 @@ __global__ void __launch_bounds__(kThreads, 4) fused_kernel(Params P) {
         }
       }
       // per-read hit counts from prefix popcounts of the answer words
-      if (P.hits) {
+      if (seg.hits) {
         __syncwarp();
         const uint32_t pc = lane < 16 ? __popc(S.k_w[lane]) : 0u;
         uint32_t incl = pc;
@@ -779,7 +789,7 @@ __global__ void __launch_bounds__(kThreads, 4) fused_kernel(Params P) {
             const uint64_t b = (re < own_hi ? re : own_hi) - p0;
             if (b > a) {
               const uint32_t cnt = bits_before((uint32_t)b) - bits_before((uint32_t)a);
-              if (cnt) atomicAdd(&P.hits[q], cnt);
+              if (cnt) atomicAdd(&seg.hits[q], cnt);
             }
           }
           const unsigned more = __ballot_sync(kFull, re < own_hi);
@@ -805,6 +815,60 @@ __global__ void __launch_bounds__(kThreads, 4) fused_kernel(Params P) {
     r_cur = r_next;
     e_batch = e_next;
     __syncwarp();
+  }
+
+}
+
+template <int W, int H, int B, bool KEY64, bool INSERT>
+__global__ void __launch_bounds__(kThreads, 4) fused_kernel(Params P) {
+  using Sm = WarpSmem<H, B, KEY64>;
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  Sm& S = reinterpret_cast<Sm*>(smem_raw)[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  unsigned long long st_valid = 0, st_runs = 0, st_pos = 0;
+
+  // Walk global iterations [a, b): split them at segment boundaries.
+  auto walk = [&](uint64_t a, uint64_t b) {
+    uint32_t si = 0;
+    if (P.segs) {  // last segment with iter_begin <= a (warp-uniform)
+      uint32_t lo = 0, hi = P.n_segs;
+      while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (P.segs[mid].iter_begin <= a) lo = mid; else hi = mid;
+      }
+      si = lo;
+    }
+    while (a < b) {
+      const Segment seg = P.segs ? P.segs[si] : P.seg0;
+      const uint64_t s_end = seg.iter_begin + seg.iters;
+      const uint64_t e = b < s_end ? b : s_end;
+      if (a < e)
+        run_range<W, H, B, KEY64, INSERT>(S, P, seg, a - seg.iter_begin, e - seg.iter_begin, lane,
+                                          st_valid, st_runs, st_pos);
+      a = e > a ? e : a;
+      if (a >= s_end) ++si;
+      if (P.segs == nullptr || si >= P.n_segs) break;
+    }
+  };
+
+  const uint64_t tw = (uint64_t)gridDim.x * kWarps;
+  const uint64_t gw = (uint64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (P.work == nullptr) {
+    // static split: each warp a contiguous share of the iterations
+    const uint64_t per = P.iters / tw, rem = P.iters % tw;
+    const uint64_t a = gw * per + (gw < rem ? gw : rem);
+    const uint64_t b = a + per + (gw < rem ? 1 : 0);
+    if (a < b) walk(a, b);
+  } else {
+    // dynamic: claim chunks of iterations from a global counter
+    while (true) {
+      uint64_t start = 0;
+      if (lane == 0) start = (uint64_t)atomicAdd(P.work, (unsigned long long)P.chunk);
+      start = __shfl_sync(kFull, start, 0);
+      if (start >= P.iters) break;
+      const uint64_t end = start + P.chunk < P.iters ? start + P.chunk : P.iters;
+      walk(start, end);
+    }
   }
 
   if (!INSERT && P.stats) {
@@ -838,11 +902,17 @@ cudaError_t launch(const Params& P, cudaStream_t st) {
   if (P.iters == 0) return cudaSuccess;
   uint64_t want_blocks = (P.iters + kWarps - 1) / kWarps;
   uint64_t cap = (uint64_t)sm_count() * blocks_per_sm;
+  if (P.grid_blocks > 0 && P.grid_blocks < cap) cap = P.grid_blocks;
   int grid = (int)(want_blocks < cap ? want_blocks : cap);
   if (grid < 1) grid = 1;
   kern<<<grid, kThreads, smem, st>>>(P);
   return cudaGetLastError();
 }
+
+// Launch a prepared parameter block (dispatch over the compiled grid).
+cudaError_t launch_params(const Params& P, bool insert, cudaStream_t st);
+// Start positions covered by one iteration for these parameters.
+int advance_of(const Geom& g);
 
 }  // namespace fused
 }  // namespace sbf

@@ -63,6 +63,15 @@ def load_library() -> ctypes.CDLL:
             "sbf_query_seqs_host": (I, [P, P, U64, P, U64, U32P, U32P]),
             "sbf_num_kmers": (I, [P, U64, I, ctypes.POINTER(U64)]),
             "sbf_last_error": (ctypes.c_char_p, []),
+            "sbf_batch_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P)]),
+            "sbf_batch_destroy": (None, [P]),
+            "sbf_batch_insert": (I, [P, P, U64, P, P, U64, P, I, P]),
+            "sbf_batch_query": (I, [P, P, U64, P, P, U64, P, U32P, U32P, I, P]),
+            "sbf_batch_set_schedule": (I, [P, I, ctypes.c_uint32, ctypes.c_uint32]),
+            "sbf_batch_get_schedule": (I, [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_uint32),
+                                           ctypes.POINTER(ctypes.c_uint32)]),
+            "sbf_batch_tune": (I, [P, I, P, U64, P, P, U64, P, U32P, U32P, P,
+                                   ctypes.POINTER(ctypes.c_float)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -237,6 +246,93 @@ class SuperBloomFilter:
             w = np.frombuffer(fh.read(), dtype="<u8")
             f.set_words(w)
         return f
+
+
+BATCH_PER_FILTER, BATCH_FUSED, BATCH_GRAPH = 0, 1, 2
+
+
+class FilterBatch:
+    """Filters with one parameter set served by one persistent launch.
+
+    Reads are grouped by filter: ``group[f]:group[f+1]`` are filter f's reads.
+    ``off`` must be given both on the device (int64 CUDA tensor) and on the
+    host (numpy uint64)."""
+
+    def __init__(self, filters):
+        lib = load_library()
+        self._filters = list(filters)  # keep them alive
+        arr = (ctypes.c_void_p * len(self._filters))(*[f.handle.value for f in self._filters])
+        h = ctypes.c_void_p()
+        _check(lib.sbf_batch_create(arr, len(self._filters), ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+
+    def close(self) -> None:
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.sbf_batch_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _host(off_host, group):
+        off_host = np.ascontiguousarray(off_host, dtype=np.uint64)
+        group = np.ascontiguousarray(group, dtype=np.uint64)
+        return off_host, group
+
+    def insert(self, seq, off, off_host, group, mode: int = BATCH_GRAPH, stream=None) -> None:
+        oh, gr = self._host(off_host, group)
+        _check(self._lib.sbf_batch_insert(self._h, _dev_ptr(seq, 1), seq.numel(), _dev_ptr(off, 8),
+                                          _host_ptr(oh), oh.size - 1, _host_ptr(gr), mode,
+                                          _stream_handle(stream)))
+
+    def query(self, seq, off, off_host, group, bits=None, hits=None, mode: int = BATCH_GRAPH,
+              stream=None):
+        import torch
+
+        oh, gr = self._host(off_host, group)
+        n = oh.size - 1
+        if bits is None:
+            bits = torch.empty((seq.numel() + 31) // 32, dtype=torch.int32, device=seq.device)
+        if hits is None:
+            hits = torch.empty(n, dtype=torch.int32, device=seq.device)
+        _check(self._lib.sbf_batch_query(self._h, _dev_ptr(seq, 1), seq.numel(), _dev_ptr(off, 8),
+                                         _host_ptr(oh), n, _host_ptr(gr), _dev_ptr(bits, 4),
+                                         _dev_ptr(hits, 4), mode, _stream_handle(stream)))
+        return bits, hits
+
+    def set_schedule(self, dynamic: bool, chunk: int, grid_blocks: int = 0) -> None:
+        _check(self._lib.sbf_batch_set_schedule(self._h, 1 if dynamic else 0, chunk, grid_blocks))
+
+    def schedule(self):
+        d, c, g = ctypes.c_int(), ctypes.c_uint32(), ctypes.c_uint32()
+        _check(self._lib.sbf_batch_get_schedule(self._h, ctypes.byref(d), ctypes.byref(c),
+                                                ctypes.byref(g)))
+        return bool(d.value), int(c.value), int(g.value)
+
+    def tune(self, seq, off, off_host, group, insert: bool = False, bits=None, hits=None,
+             stream=None) -> float:
+        """Autotune the schedule on this call; returns the best time in ms."""
+        import torch
+
+        oh, gr = self._host(off_host, group)
+        n = oh.size - 1
+        if not insert:
+            if bits is None:
+                bits = torch.empty((seq.numel() + 31) // 32, dtype=torch.int32, device=seq.device)
+            if hits is None:
+                hits = torch.empty(n, dtype=torch.int32, device=seq.device)
+        best = ctypes.c_float()
+        _check(self._lib.sbf_batch_tune(self._h, 1 if insert else 0, _dev_ptr(seq, 1), seq.numel(),
+                                        _dev_ptr(off, 8), _host_ptr(oh), n, _host_ptr(gr),
+                                        _dev_ptr(bits, 4), _dev_ptr(hits, 4),
+                                        _stream_handle(stream), ctypes.byref(best)))
+        return float(best.value)
 
 
 def num_kmers(off: np.ndarray, k: int) -> int:

@@ -330,3 +330,103 @@ def mixed_query_reads(genome: np.ndarray, n_sampled: int, n_random: int, length:
     s2, _ = random_reads(n_random, length, seed + 1)
     seq = np.concatenate([s1, s2])
     return seq, fixed_length_offsets(n_sampled + n_random, length)
+
+
+def sample_variable_reads(genome: np.ndarray, lengths: np.ndarray, error_rate: float, seed: int,
+                          stream_base: int = 0) -> np.ndarray:
+    """Concatenated reads of the given lengths (each clipped to the genome)
+    from uniform positions on a random strand with substitution errors."""
+    n = genome.size
+    lengths = np.minimum(np.asarray(lengths, dtype=np.int64), n)
+    total = int(lengths.sum())
+    out = np.empty(total, dtype=np.uint8)
+    if total == 0:
+        return out
+    starts = randint(seed, 71 + stream_base, lengths.size, 0, 1 << 62) % (n - lengths + 1)
+    strand = randint(seed, 72 + stream_base, lengths.size, 0, 2).astype(bool)
+    cum = np.zeros(lengths.size + 1, dtype=np.int64)
+    np.cumsum(lengths, out=cum[1:])
+    step = 1 << 24
+    r0 = 0
+    while r0 < lengths.size:
+        r1 = int(np.searchsorted(cum, cum[r0] + step, side="right")) - 1
+        r1 = max(r1, r0 + 1)
+        L = lengths[r0:r1]
+        base = cum[r0]
+        rel = np.arange(int(cum[r1] - base), dtype=np.int64)
+        owner = np.repeat(np.arange(r0, r1), L)
+        within = rel - (cum[owner] - base)
+        fwd = starts[owner] + within
+        rev = starts[owner] + (lengths[owner] - 1 - within)
+        sb = strand[owner]
+        piece = genome[np.where(sb, rev, fwd)]
+        piece = np.where(sb, _COMPLEMENT[piece], piece)
+        out[base:base + piece.size] = piece
+        r0 = r1
+    u = u64(seed, 73 + stream_base, 0, total)
+    idx = np.nonzero((u >> np.uint64(32)) < np.uint64(int(error_rate * 2.0 ** 32)))[0]
+    if idx.size:
+        sub = 1 + (((u[idx] & np.uint64(0xFFFFFFFF)) * np.uint64(3)) >> np.uint64(32)).astype(np.int64)
+        code = np.searchsorted(_ACGT, out[idx])
+        out[idx] = _ACGT[(code + sub) % 4]
+    return out
+
+
+def batched_workload(n_filters: int = 256, exp_lo: int = 20, exp_hi: int = 28,
+                     genome_lo: float = 1e6, genome_hi: float = 50e6, n_reads: int = 5_000_000,
+                     seed: int = 4, read_cap: int = 100_000):
+    """Many independent filters queried in one launch.
+
+    Filter sizes 2^e bits with e uniform in [exp_lo, exp_hi]; genome lengths
+    log-uniform in [genome_lo, genome_hi] (uniform random DNA); both lists
+    sorted ascending and paired so bits per k-mer stay in a sane range.  Read
+    lengths clip(round(lognormal(ln 150, 1.5)), 1, read_cap); each read goes
+    to a uniform filter; half are sampled from that filter's genome with 1%
+    errors, half are random.  Reads are grouped by filter.
+
+    Returns dict(bits, genomes, gseq, goff, ggroup, seq, off, group)."""
+    exps = np.sort(randint(seed, 81, n_filters, exp_lo, exp_hi + 1))
+    glen = np.sort(np.exp(np.log(genome_lo) + uniform01(seed, 82, 0, n_filters)
+                          * (np.log(genome_hi) - np.log(genome_lo))).astype(np.int64))
+    bits = [int(1) << int(e) for e in exps]
+    genomes = [uniform_dna(int(L), seed * 1000 + f) for f, L in enumerate(glen)]
+    lens = lognormal_lengths(n_reads, 150, 1.5, 1, read_cap, seed + 7)
+    owner = randint(seed, 83, n_reads, 0, n_filters)
+    sampled = randint(seed, 84, n_reads, 0, 2).astype(bool)
+    order = np.argsort(owner, kind="stable")
+    owner, lens, sampled = owner[order], lens[order], sampled[order]
+    group = np.searchsorted(owner, np.arange(n_filters + 1)).astype(np.uint64)
+    parts = []
+    for f in range(n_filters):
+        a, b = int(group[f]), int(group[f + 1])
+        if a == b:
+            continue
+        L, smp = lens[a:b], sampled[a:b]
+        piece_s = sample_variable_reads(genomes[f], L[smp], 0.01, seed + 11 * f + 1)
+        piece_r = uniform_dna(int(L[~smp].sum()), seed * 7919 + f)
+        # interleave in read order: sampled and random reads keep their slots
+        Lc = np.minimum(L, np.where(smp, genomes[f].size, L))
+        cum_s = np.concatenate([[0], np.cumsum(Lc[smp])])
+        cum_r = np.concatenate([[0], np.cumsum(L[~smp])])
+        out = np.empty(int(Lc.sum()), dtype=np.uint8)
+        pos = 0
+        si = ri = 0
+        for is_s, l in zip(smp, Lc):
+            if is_s:
+                out[pos:pos + l] = piece_s[cum_s[si]:cum_s[si + 1]]
+                si += 1
+            else:
+                out[pos:pos + l] = piece_r[cum_r[ri]:cum_r[ri + 1]]
+                ri += 1
+            pos += l
+        lens[a:b] = Lc
+        parts.append(out)
+    seq = np.concatenate(parts) if parts else np.zeros(0, np.uint8)
+    off = np.zeros(n_reads + 1, dtype=np.uint64)
+    np.cumsum(lens, out=off[1:])
+    gseq = np.concatenate(genomes)
+    gl = np.array([g.size for g in genomes], dtype=np.uint64)
+    goff = np.zeros(n_filters + 1, dtype=np.uint64)
+    np.cumsum(gl, out=goff[1:])
+    return dict(bits=bits, genomes=genomes, gseq=gseq, goff=goff,
+                ggroup=np.arange(n_filters + 1, dtype=np.uint64), seq=seq, off=off, group=group)
