@@ -29,6 +29,7 @@ struct sbf_batch {
   unsigned long long* d_work = nullptr;
   cudaEvent_t upload_done = nullptr;
   bool upload_pending = false;
+  cudaStream_t capture_stream = nullptr;  // graphs are captured here (never the legacy stream)
   // schedule (sbf_batch_tune picks it)
   int dynamic = 1;
   uint32_t chunk = 4;
@@ -248,10 +249,11 @@ int run_batch(sbf_batch* b, bool insert, const uint8_t* d_seq, uint64_t seq_len,
     if ((e = enqueue_fused(b, insert, d_seq, seq_len, n_reads, d_bits, d_hits, n_segs, 0, st)) != cudaSuccess)
       return cuda_fail(e, "kernel setup");
     cudaGraph_t g = nullptr;
-    if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    cudaStream_t cs = b->capture_stream;
+    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
       return cuda_fail(e, "begin capture");
-    cudaError_t le = enqueue_fused(b, insert, d_seq, seq_len, n_reads, d_bits, d_hits, n_segs, iters, st);
-    e = cudaStreamEndCapture(st, &g);
+    cudaError_t le = enqueue_fused(b, insert, d_seq, seq_len, n_reads, d_bits, d_hits, n_segs, iters, cs);
+    e = cudaStreamEndCapture(cs, &g);
     if (le != cudaSuccess || e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       return cuda_fail(le != cudaSuccess ? le : e, "graph capture");
@@ -295,7 +297,8 @@ int sbf_batch_create(sbf_filter* const* filters, int n_filters, sbf_batch** out)
   b->device = filters[0]->device;
   DeviceGuard dg(b->device);
   if (cudaMalloc(&b->d_work, sizeof(unsigned long long)) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->upload_done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&b->upload_done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(b->d_work);
     delete b;
@@ -314,6 +317,7 @@ void sbf_batch_destroy(sbf_batch* b) {
   cudaFreeHost(b->h_segs);
   cudaFree(b->d_work);
   if (b->upload_done) cudaEventDestroy(b->upload_done);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   delete b;
 }
 
