@@ -433,6 +433,7 @@ def run_batched(args):
         return e0.elapsed_time(e1) / reps
 
     res = {}
+    tuned_ins_ms = batch.tune(dg, dgo, w["goff"], w["ggroup"], insert=True)
     for name, mode in [("per_filter", BATCH_PER_FILTER), ("graph", BATCH_GRAPH)]:
         res[f"insert_ms_{name}"] = timed(
             lambda: batch.insert(dg, dgo, w["goff"], w["ggroup"], mode=mode), args.steps)
@@ -447,6 +448,7 @@ def run_batched(args):
     same = all(torch.equal(answers[n][0], answers["per_filter"][0]) and
                torch.equal(answers[n][1], answers["per_filter"][1]) for n in answers)
     dyn, chunk, grid = batch.schedule()
+    idyn, ichunk, igrid = batch.schedule(insert=True)
     line = {"workload": "batched: 256 filters of 2^20-2^28 bits (log-uniform sizes) built from "
                         "1-50 Mbp uniform genomes (log-uniform), 5M reads of lognormal lengths "
                         "(median 150 bp, sigma 1.5, cap 100 kb), half sampled with 1% errors",
@@ -456,8 +458,10 @@ def run_batched(args):
             "query_kmers_per_s_per_filter": q_kmers / (res["query_ms_per_filter"] / 1e3),
             "insert_kmers_per_s_graph": ins_kmers / (res["insert_ms_graph"] / 1e3),
             "insert_kmers_per_s_per_filter": ins_kmers / (res["insert_ms_per_filter"] / 1e3),
-            "tuned_schedule": {"dynamic": dyn, "chunk": chunk, "grid_blocks": grid,
-                               "tuned_query_ms": tuned_ms},
+            "tuned_schedule": {"query": {"dynamic": dyn, "chunk": chunk, "grid_blocks": grid,
+                                         "tuned_ms": tuned_ms},
+                               "insert": {"dynamic": idyn, "chunk": ichunk, "grid_blocks": igrid,
+                                          "tuned_ms": tuned_ins_ms}},
             "answers_identical_across_modes": same}
     print(json.dumps(line), flush=True)
     return 0

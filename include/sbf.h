@@ -170,15 +170,18 @@ int sbf_batch_insert(sbf_batch* b, const uint8_t* d_seq, uint64_t seq_len, const
 int sbf_batch_query(sbf_batch* b, const uint8_t* d_seq, uint64_t seq_len, const uint64_t* d_off,
                     const uint64_t* h_off, uint64_t n_reads, const uint64_t* h_group,
                     uint32_t* d_kmer_bits, uint32_t* d_read_hits, int mode, sbf_stream_t stream);
-/* Schedule of the persistent launch: dynamic = 0 splits the iterations (496
- * start positions each) into one contiguous share per warp; dynamic = 1 lets
- * warps claim `chunk` iterations at a time from a device counter;
- * grid_blocks caps the blocks (0 = full occupancy). */
-int sbf_batch_set_schedule(sbf_batch* b, int dynamic, uint32_t chunk, uint32_t grid_blocks);
-int sbf_batch_get_schedule(const sbf_batch* b, int* dynamic, uint32_t* chunk,
+/* Schedule of the persistent query (insert = 0) or insert (insert = 1)
+ * launch: dynamic = 0 splits the iterations (496 start positions each) into
+ * one contiguous share per warp; dynamic = 1 lets warps claim `chunk`
+ * iterations at a time from a device counter; grid_blocks caps the blocks
+ * (0 = full occupancy). */
+int sbf_batch_set_schedule(sbf_batch* b, int insert, int dynamic, uint32_t chunk,
+                           uint32_t grid_blocks);
+int sbf_batch_get_schedule(const sbf_batch* b, int insert, int* dynamic, uint32_t* chunk,
                            uint32_t* grid_blocks);
-/* Autotuner: times every candidate schedule on this exact call (insert != 0:
- * the insert) with CUDA events, keeps the fastest and returns its time in
+/* Autotuner: times every candidate schedule (static split; dynamic chunks of
+ * 4 to 1024 iterations) on this exact call (insert != 0: the insert) with
+ * CUDA events, keeps the fastest for that operation and returns its time in
  * *best_ms.  Synchronises; the call's outputs are left as a normal call
  * leaves them. */
 int sbf_batch_tune(sbf_batch* b, int insert, const uint8_t* d_seq, uint64_t seq_len,

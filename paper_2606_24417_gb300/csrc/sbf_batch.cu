@@ -30,10 +30,12 @@ struct sbf_batch {
   cudaEvent_t upload_done = nullptr;
   bool upload_pending = false;
   cudaStream_t capture_stream = nullptr;  // graphs are captured here (never the legacy stream)
-  // schedule (sbf_batch_tune picks it)
-  int dynamic = 1;
-  uint32_t chunk = 4;
-  uint32_t grid_blocks = 0;
+  // schedules of the query [0] and insert [1] launches (sbf_batch_tune picks them)
+  struct Sched {
+    int dynamic;
+    uint32_t chunk;
+    uint32_t grid_blocks;
+  } sched[2] = {{1, 16, 0}, {1, 64, 0}};
   // captured graph and the launch it encodes
   cudaGraphExec_t graph = nullptr;
   struct Key {
@@ -161,7 +163,8 @@ cudaError_t enqueue_fused(sbf_batch* b, bool insert, const uint8_t* seq, uint64_
       return e;
     if (hits && n_reads && (e = cudaMemsetAsync(hits, 0, n_reads * 4, st)) != cudaSuccess) return e;
   }
-  if (b->dynamic && (e = cudaMemsetAsync(b->d_work, 0, sizeof(unsigned long long), st)) != cudaSuccess)
+  const sbf_batch::Sched& sc = b->sched[insert ? 1 : 0];
+  if (sc.dynamic && (e = cudaMemsetAsync(b->d_work, 0, sizeof(unsigned long long), st)) != cudaSuccess)
     return e;
   Params P{};
   P.g = b->geom;
@@ -172,9 +175,9 @@ cudaError_t enqueue_fused(sbf_batch* b, bool insert, const uint8_t* seq, uint64_
   P.segs = b->d_segs;
   P.n_segs = n_segs;
   P.iters = iters;
-  P.work = b->dynamic ? b->d_work : nullptr;
-  P.chunk = b->chunk > 0 ? b->chunk : 1;
-  P.grid_blocks = b->grid_blocks;
+  P.work = sc.dynamic ? b->d_work : nullptr;
+  P.chunk = sc.chunk > 0 ? sc.chunk : 1;
+  P.grid_blocks = sc.grid_blocks;
   return sbf::fused::launch_params(P, insert, st);
 }
 
@@ -237,9 +240,9 @@ int run_batch(sbf_batch* b, bool insert, const uint8_t* d_seq, uint64_t seq_len,
   key.n_reads = n_reads;
   key.n_segs = n_segs;
   key.iters = iters;
-  key.dynamic = b->dynamic;
-  key.chunk = b->chunk;
-  key.grid_blocks = b->grid_blocks;
+  key.dynamic = b->sched[insert ? 1 : 0].dynamic;
+  key.chunk = b->sched[insert ? 1 : 0].chunk;
+  key.grid_blocks = b->sched[insert ? 1 : 0].grid_blocks;
   if (!b->graph || !(key == b->key)) {
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
@@ -321,21 +324,22 @@ void sbf_batch_destroy(sbf_batch* b) {
   delete b;
 }
 
-int sbf_batch_set_schedule(sbf_batch* b, int dynamic, uint32_t chunk, uint32_t grid_blocks) {
+int sbf_batch_set_schedule(sbf_batch* b, int insert, int dynamic, uint32_t chunk,
+                           uint32_t grid_blocks) {
   sbf::clear_error();
   if (!b || chunk == 0) return fail(SBF_EINVAL, "bad argument");
-  b->dynamic = dynamic ? 1 : 0;
-  b->chunk = chunk;
-  b->grid_blocks = grid_blocks;
+  b->sched[insert ? 1 : 0] = sbf_batch::Sched{dynamic ? 1 : 0, chunk, grid_blocks};
   return SBF_OK;
 }
 
-int sbf_batch_get_schedule(const sbf_batch* b, int* dynamic, uint32_t* chunk, uint32_t* grid_blocks) {
+int sbf_batch_get_schedule(const sbf_batch* b, int insert, int* dynamic, uint32_t* chunk,
+                           uint32_t* grid_blocks) {
   sbf::clear_error();
   if (!b) return fail(SBF_EINVAL, "batch is NULL");
-  if (dynamic) *dynamic = b->dynamic;
-  if (chunk) *chunk = b->chunk;
-  if (grid_blocks) *grid_blocks = b->grid_blocks;
+  const sbf_batch::Sched& sc = b->sched[insert ? 1 : 0];
+  if (dynamic) *dynamic = sc.dynamic;
+  if (chunk) *chunk = sc.chunk;
+  if (grid_blocks) *grid_blocks = sc.grid_blocks;
   return SBF_OK;
 }
 
@@ -363,14 +367,11 @@ int sbf_batch_tune(sbf_batch* b, int insert, const uint8_t* d_seq, uint64_t seq_
   if (!b) return fail(SBF_EINVAL, "batch is NULL");
   DeviceGuard dg(b->device);
   cudaStream_t st = (cudaStream_t)stream;
-  struct Cand {
-    int dynamic;
-    uint32_t chunk;
-    uint32_t grid;
-  };
+  using Cand = sbf_batch::Sched;
   const uint32_t full = 0;  // full occupancy
-  const Cand cands[] = {{0, 1, full}, {1, 1, full}, {1, 2, full}, {1, 4, full},
-                        {1, 8, full}, {1, 16, full}, {1, 32, full}};
+  const Cand cands[] = {{0, 1, full},  {1, 4, full},   {1, 16, full},
+                        {1, 64, full}, {1, 256, full}, {1, 1024, full}};
+  sbf_batch::Sched& sc = b->sched[insert ? 1 : 0];
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -378,9 +379,7 @@ int sbf_batch_tune(sbf_batch* b, int insert, const uint8_t* d_seq, uint64_t seq_
   Cand pick = cands[0];
   int rc = SBF_OK;
   for (const Cand& c : cands) {
-    b->dynamic = c.dynamic;
-    b->chunk = c.chunk;
-    b->grid_blocks = c.grid;
+    sc = c;
     float t_min = 1e30f;
     for (int rep = 0; rep < 4 && rc == SBF_OK; ++rep) {
       cudaEventRecord(e0, st);
@@ -400,9 +399,7 @@ int sbf_batch_tune(sbf_batch* b, int insert, const uint8_t* d_seq, uint64_t seq_
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->dynamic = pick.dynamic;
-  b->chunk = pick.chunk;
-  b->grid_blocks = pick.grid;
+  sc = pick;
   if (best_ms) *best_ms = best;
   return rc;
 }

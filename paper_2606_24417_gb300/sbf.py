@@ -67,8 +67,8 @@ def load_library() -> ctypes.CDLL:
             "sbf_batch_destroy": (None, [P]),
             "sbf_batch_insert": (I, [P, P, U64, P, P, U64, P, I, P]),
             "sbf_batch_query": (I, [P, P, U64, P, P, U64, P, U32P, U32P, I, P]),
-            "sbf_batch_set_schedule": (I, [P, I, ctypes.c_uint32, ctypes.c_uint32]),
-            "sbf_batch_get_schedule": (I, [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_uint32),
+            "sbf_batch_set_schedule": (I, [P, I, I, ctypes.c_uint32, ctypes.c_uint32]),
+            "sbf_batch_get_schedule": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_uint32),
                                            ctypes.POINTER(ctypes.c_uint32)]),
             "sbf_batch_tune": (I, [P, I, P, U64, P, P, U64, P, U32P, U32P, P,
                                    ctypes.POINTER(ctypes.c_float)]),
@@ -306,13 +306,15 @@ class FilterBatch:
                                          _dev_ptr(hits, 4), mode, _stream_handle(stream)))
         return bits, hits
 
-    def set_schedule(self, dynamic: bool, chunk: int, grid_blocks: int = 0) -> None:
-        _check(self._lib.sbf_batch_set_schedule(self._h, 1 if dynamic else 0, chunk, grid_blocks))
+    def set_schedule(self, dynamic: bool, chunk: int, grid_blocks: int = 0,
+                     insert: bool = False) -> None:
+        _check(self._lib.sbf_batch_set_schedule(self._h, 1 if insert else 0, 1 if dynamic else 0,
+                                                chunk, grid_blocks))
 
-    def schedule(self):
+    def schedule(self, insert: bool = False):
         d, c, g = ctypes.c_int(), ctypes.c_uint32(), ctypes.c_uint32()
-        _check(self._lib.sbf_batch_get_schedule(self._h, ctypes.byref(d), ctypes.byref(c),
-                                                ctypes.byref(g)))
+        _check(self._lib.sbf_batch_get_schedule(self._h, 1 if insert else 0, ctypes.byref(d),
+                                                ctypes.byref(c), ctypes.byref(g)))
         return bool(d.value), int(c.value), int(g.value)
 
     def tune(self, seq, off, off_host, group, insert: bool = False, bits=None, hits=None,
