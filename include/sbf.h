@@ -189,6 +189,46 @@ int sbf_batch_tune(sbf_batch* b, int insert, const uint8_t* d_seq, uint64_t seq_
                    const uint64_t* h_group, uint32_t* d_kmer_bits, uint32_t* d_read_hits,
                    sbf_stream_t stream, float* best_ms);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop around one resident filter (continuous batching).
+ * Not in the paper.
+ *
+ * sbf_server_create: the filter (with a fused kernel) stays resident; the
+ *   server owns read_budget_bytes of device memory for request reads (plus a
+ *   quarter of that for offsets and hit counts) and a worker thread.  Queued
+ *   requests are admitted while that memory has room, every request admitted
+ *   at one moment (at most max_per_launch of them, 1..65536) is served by ONE
+ *   kernel launch (one segment each), and up to max_inflight (1..16)
+ *   launches run at once on separate streams, so requests that arrive while
+ *   others run overlap with them.  max_per_launch = 1 gives one launch per
+ *   request, the baseline continuous batching is measured against.
+ * sbf_server_submit: queue one request of host reads (offsets as in
+ *   sbf_query_seqs, off[0] = 0).  h_read_hits (n_reads) and h_kmer_bits
+ *   (ceil(seq_len/32) words, may be NULL) receive exactly what
+ *   sbf_query_seqs would write.  All host buffers must stay valid until the
+ *   request is waited for; pinned buffers make the copies asynchronous.  A
+ *   request larger than the budget is refused (SBF_EINVAL).  Thread-safe.
+ * sbf_server_wait: block until the request is done or timeout_s passes
+ *   (SBF_ETIMEOUT); on success the ticket is released and *latency_s (may be
+ *   NULL) is the time from submission to completion.
+ * sbf_server_stats: latency percentiles of the requests completed since the
+ *   last reset, and k-mers served per second from the first submission to
+ *   the last completion.
+ * sbf_server_destroy: finishes queued and running requests, then frees.
+ * ------------------------------------------------------------------------- */
+typedef struct sbf_server sbf_server;
+
+int sbf_server_create(const sbf_filter* f, uint64_t read_budget_bytes, int max_inflight,
+                      uint32_t max_per_launch, sbf_server** out);
+void sbf_server_destroy(sbf_server* s);
+int sbf_server_submit(sbf_server* s, const uint8_t* h_seq, uint64_t seq_len, const uint64_t* h_off,
+                      uint64_t n_reads, uint32_t* h_read_hits, uint32_t* h_kmer_bits,
+                      uint64_t* ticket);
+int sbf_server_wait(sbf_server* s, uint64_t ticket, double timeout_s, double* latency_s);
+int sbf_server_stats(sbf_server* s, uint64_t* completed, double* p50_s, double* p99_s,
+                     double* mean_s, double* kmers_per_s, uint64_t* launches);
+int sbf_server_reset_stats(sbf_server* s);
+
 /* Number of k-mer start positions sum_r max(0, len_r - k + 1) of a host
  * offset table (valid or not). */
 int sbf_num_kmers(const uint64_t* h_off, uint64_t n_reads, int k, uint64_t* out);

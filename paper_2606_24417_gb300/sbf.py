@@ -63,6 +63,14 @@ def load_library() -> ctypes.CDLL:
             "sbf_query_seqs_host": (I, [P, P, U64, P, U64, U32P, U32P]),
             "sbf_num_kmers": (I, [P, U64, I, ctypes.POINTER(U64)]),
             "sbf_last_error": (ctypes.c_char_p, []),
+            "sbf_server_create": (I, [P, U64, I, ctypes.c_uint32, ctypes.POINTER(P)]),
+            "sbf_server_destroy": (None, [P]),
+            "sbf_server_submit": (I, [P, P, U64, P, U64, U32P, U32P, ctypes.POINTER(U64)]),
+            "sbf_server_wait": (I, [P, U64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+            "sbf_server_stats": (I, [P, ctypes.POINTER(U64), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(U64)]),
+            "sbf_server_reset_stats": (I, [P]),
             "sbf_batch_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P)]),
             "sbf_batch_destroy": (None, [P]),
             "sbf_batch_insert": (I, [P, P, U64, P, P, U64, P, I, P]),
@@ -335,6 +343,73 @@ class FilterBatch:
                                         _dev_ptr(bits, 4), _dev_ptr(hits, 4),
                                         _stream_handle(stream), ctypes.byref(best)))
         return float(best.value)
+
+
+class FilterServer:
+    """Continuous-batching request loop around one resident filter.
+
+    ``submit`` queues host reads and returns a ticket; ``wait`` blocks (with a
+    timeout) until the answers are in the caller's buffers.  Buffers passed
+    to ``submit`` are kept alive here until waited for."""
+
+    def __init__(self, filt: "SuperBloomFilter", read_budget_bytes: int = 256 << 20,
+                 max_inflight: int = 3, max_per_launch: int = 4096):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.sbf_server_create(filt.handle, read_budget_bytes, max_inflight, max_per_launch,
+                                     ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+        self._filter = filt
+        self._keep = {}
+        self._lock = threading.Lock()
+
+    def close(self) -> None:
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.sbf_server_destroy(h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, seq: np.ndarray, off: np.ndarray, want_bits: bool = False):
+        seq = np.ascontiguousarray(seq, dtype=np.uint8)
+        off = np.ascontiguousarray(off, dtype=np.uint64)
+        n = off.size - 1
+        hits = np.empty(n, dtype=np.uint32)
+        bits = np.empty((seq.size + 31) // 32, dtype=np.uint32) if want_bits else None
+        t = ctypes.c_uint64()
+        _check(self._lib.sbf_server_submit(self._h, _host_ptr(seq), seq.size, _host_ptr(off), n,
+                                           _host_ptr(hits), _host_ptr(bits), ctypes.byref(t)))
+        with self._lock:
+            self._keep[t.value] = (seq, off, hits, bits)
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        """Returns (hits, bits or None, latency seconds)."""
+        lat = ctypes.c_double()
+        rc = self._lib.sbf_server_wait(self._h, ticket, timeout_s, ctypes.byref(lat))
+        with self._lock:
+            keep = self._keep.pop(ticket, None) if rc != -5 else self._keep.get(ticket)
+        _check(rc)
+        return keep[2], keep[3], float(lat.value)
+
+    def stats(self) -> dict:
+        c, l = ctypes.c_uint64(), ctypes.c_uint64()
+        p50, p99, mean, kps = (ctypes.c_double() for _ in range(4))
+        _check(self._lib.sbf_server_stats(self._h, ctypes.byref(c), ctypes.byref(p50),
+                                          ctypes.byref(p99), ctypes.byref(mean), ctypes.byref(kps),
+                                          ctypes.byref(l)))
+        return {"completed": int(c.value), "p50_s": p50.value, "p99_s": p99.value,
+                "mean_s": mean.value, "kmers_per_s": kps.value, "launches": int(l.value)}
+
+    def reset_stats(self) -> None:
+        _check(self._lib.sbf_server_reset_stats(self._h))
 
 
 def num_kmers(off: np.ndarray, k: int) -> int:

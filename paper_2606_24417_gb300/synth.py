@@ -148,23 +148,43 @@ def _markov_table(order: int, gc: float, seed: int, alpha: int = MARKOV_ALPHA) -
     return tilt(math.sqrt(lo * hi))
 
 
-def markov_dna(n: int, order: int, gc: float, seed: int, n_chains: int = 4096) -> np.ndarray:
+def markov_dna(n: int, order: int, gc: float, seed: int, n_chains: int | None = None) -> np.ndarray:
     """Order-`order` Markov DNA of length n, run as n_chains independent
-    segments (vectorised across segments) that are concatenated."""
+    segments (vectorised across segments, groups of segments on threads)
+    that are concatenated.  The next base is looked up from the top 16 bits
+    of a uniform draw in a per-context quantile table (probabilities resolved
+    to 2^-16).  Step t of chain c draws counter t * n_chains + c, so the
+    result does not depend on the thread grouping."""
     P = _markov_table(order, gc, seed)
     cum = np.cumsum(P, axis=1)
     cum[:, -1] = 1.0
     n_ctx = 4 ** order
+    q = (np.arange(1 << 16, dtype=np.float64) + 0.5) / (1 << 16)
+    table = np.empty((n_ctx, 1 << 16), dtype=np.uint8)
+    for c in range(n_ctx):
+        table[c] = np.searchsorted(cum[c], q, side="right")
+    table = np.minimum(table, 3).reshape(-1)
+    if n_chains is None:  # about 256 steps: large vector operations run well on threads
+        n_chains = max(4096, -(-n // 256))
     n_chains = max(1, min(n_chains, n))
     seg = (n + n_chains - 1) // n_chains
-    codes = np.empty((n_chains, seg), dtype=np.uint8)
-    ctx = randint(seed, 11, n_chains, 0, n_ctx)
-    for t in range(seg):
-        u = uniform01(seed, 12, t * n_chains, n_chains)
-        c = (u[:, None] >= cum[ctx]).sum(axis=1).astype(np.int64)
-        codes[:, t] = c
-        ctx = (ctx * 4 + c) % n_ctx
-    return _ACGT[codes.reshape(-1)[:n]]
+    codes = np.empty((seg, n_chains), dtype=np.uint8)
+    ctx0 = randint(seed, 11, n_chains, 0, n_ctx)
+    n_groups = max(1, min(os.cpu_count() or 1, 32, n_chains // 1024))
+    bounds = np.linspace(0, n_chains, n_groups + 1).astype(np.int64)
+    s48 = np.uint64(48)
+
+    def run(gi):
+        c0, c1 = int(bounds[gi]), int(bounds[gi + 1])
+        ctx = ctx0[c0:c1].astype(np.int64)
+        for t in range(seg):
+            u = (u64(seed, 12, t * n_chains + c0, c1 - c0) >> s48).astype(np.int64)
+            c = table[ctx * (1 << 16) + u]
+            codes[t, c0:c1] = c
+            ctx = (ctx * 4 + c) % n_ctx
+
+    _parallel(run, range(n_groups))
+    return _ACGT[codes.T.reshape(-1)[:n]]
 
 
 def gc_fraction(x: np.ndarray) -> float:
@@ -198,33 +218,58 @@ def add_diverged_repeats(genome: np.ndarray, frac: float, n_families: int, min_l
                          gc: float = 0.41) -> np.ndarray:
     """Interspersed repeats: n_families consensus sequences (log-uniform lengths,
     drawn from the same Markov chain), copied with independent substitutions
-    and random strand until about frac of the genome is covered."""
+    and random strand until about frac of the genome is covered.  Copies are
+    written in order (a later copy overwrites an earlier one)."""
     g = genome.copy()
     n = g.size
     ll = np.exp(np.log(min_len) + uniform01(seed, 31, 0, n_families)
                 * (np.log(max_len) - np.log(min_len)))
     flen = np.maximum(min_len, ll.astype(np.int64))
     fam_src = markov_dna(int(flen.sum()), order, gc, seed + 1, n_chains=min(4096, n_families))
-    starts = np.concatenate([[0], np.cumsum(flen)[:-1]])
+    fstart = np.concatenate([[0], np.cumsum(flen)[:-1]])
     mean = float(flen.mean())
     count = int(round(frac * n / mean))
     fam = randint(seed, 32, count, 0, n_families)
     dst = randint(seed, 33, count, 0, max(1, n - max_len))
-    strand = randint(seed, 34, count, 0, 2)
-    pos_ctr = 0
-    for f, b, st in zip(fam, dst, strand):
-        L = int(flen[f])
-        piece = fam_src[starts[f]:starts[f] + L].copy()
-        u = uniform01(seed, 35, pos_ctr, L)
-        sub = randint(seed + pos_ctr, 36, L, 1, 4)
-        pos_ctr += L
-        hit = u < divergence
-        if hit.any():
-            code = np.searchsorted(_ACGT, piece[hit])
-            piece[hit] = _ACGT[(code + sub[hit]) % 4]
-        if st:
-            piece = reverse_complement(piece)
-        g[b:b + L] = piece
+    strand = randint(seed, 34, count, 0, 2).astype(bool)
+    L = flen[fam]
+    cum = np.zeros(count + 1, dtype=np.int64)
+    np.cumsum(L, out=cum[1:])
+    # chunks of whole copies, about 2^23 bases each
+    cuts = [0]
+    while cuts[-1] < count:
+        nxt = int(np.searchsorted(cum, cum[cuts[-1]] + (1 << 23), side="right")) - 1
+        cuts.append(max(nxt, cuts[-1] + 1))
+    chunks = list(zip(cuts[:-1], cuts[1:]))
+    results = [None] * len(chunks)
+    thr = np.uint64(int(divergence * 2.0 ** 32))
+
+    def build(ci):
+        a, b = chunks[ci]
+        base = cum[a]
+        m = int(cum[b] - base)
+        owner = np.repeat(np.arange(a, b), L[a:b])
+        within = np.arange(m, dtype=np.int64) - (cum[owner] - base)
+        st = strand[owner]
+        src = fstart[fam[owner]] + np.where(st, L[owner] - 1 - within, within)
+        vals = fam_src[src]
+        vals = np.where(st, _COMPLEMENT[vals], vals)
+        u = u64(seed, 35, int(base), m)
+        hit = np.nonzero((u >> np.uint64(32)) < thr)[0]
+        if hit.size:
+            sub = 1 + (((u[hit] & np.uint64(0xFFFFFFFF)) * np.uint64(3)) >> np.uint64(32)).astype(np.int64)
+            code = np.searchsorted(_ACGT, vals[hit])
+            vals[hit] = _ACGT[(code + sub) % 4]
+        results[ci] = (dst[owner] + within, vals)
+
+    step = max(1, min(32, os.cpu_count() or 1))
+    for c0 in range(0, len(chunks), step):  # bounded memory: build a group, apply it in order
+        ids = range(c0, min(len(chunks), c0 + step))
+        _parallel(build, ids)
+        for ci in ids:
+            pos, vals = results[ci]
+            g[pos] = vals
+            results[ci] = None
     return g
 
 
@@ -319,7 +364,7 @@ def bacterial_genome(n: int = 100_000_000, seed: int = 2) -> np.ndarray:
 def human_like_genome(n: int = 3_100_000_000, seed: int = 5) -> np.ndarray:
     """Order-5 Markov genome at GC 41% with 45% covered by interspersed copies
     of 500 repeat families (300 bp - 6 kb, 10% divergence, random strand)."""
-    g = markov_dna(n, 5, 0.41, seed, n_chains=65536)
+    g = markov_dna(n, 5, 0.41, seed)
     return add_diverged_repeats(g, 0.45, 500, 300, 6000, 0.10, seed + 100)
 
 
