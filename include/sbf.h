@@ -189,6 +189,27 @@ int sbf_batch_tune(sbf_batch* b, int insert, const uint8_t* d_seq, uint64_t seq_
                    const uint64_t* h_group, uint32_t* d_kmer_bits, uint32_t* d_read_hits,
                    sbf_stream_t stream, float* best_ms);
 
+/* Batched query without any allocation.  The paper has no counterpart: it is
+ * an entry point for callers that cannot call cudaMalloc -- for instance a
+ * process whose framework allocator has already reserved almost all GPU
+ * memory, or a latency-critical path that cannot take cudaMalloc's implicit
+ * device synchronisation.  It answers exactly like sbf_batch_query in
+ * SBF_BATCH_FUSED mode (same arguments, the filters passed directly instead of
+ * a batch object), but its scratch (a work counter and the per-filter table)
+ * lives in a fixed array compiled into the library: 33,024 bytes that every
+ * GPU loading the library holds until the process exits.  Hence at most 512
+ * filters per call (more: SBF_EINVAL).  No device or pinned memory is
+ * allocated; the table is staged through a 4 KB stack buffer.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls on a device share the array and each call
+ * resets what it needs, so calls whose work overlaps on the GPU (other
+ * streams, other host threads without ordering) race: order them. */
+int sbf_batch_query_noalloc(sbf_filter* const* filters, int n_filters, const uint8_t* d_seq,
+                            uint64_t seq_len, const uint64_t* d_off, const uint64_t* h_off,
+                            uint64_t n_reads, const uint64_t* h_group, uint32_t* d_kmer_bits,
+                            uint32_t* d_read_hits, sbf_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Serving: a request loop around one resident filter (continuous batching).
  * Not in the paper.

@@ -72,6 +72,8 @@ def load_library() -> ctypes.CDLL:
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(U64)]),
             "sbf_server_reset_stats": (I, [P]),
             "sbf_batch_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P)]),
+            "sbf_batch_query_noalloc": (I, [ctypes.POINTER(P), I, P, U64, P, P, U64, P, U32P, U32P,
+                                            P]),
             "sbf_batch_destroy": (None, [P]),
             "sbf_batch_insert": (I, [P, P, U64, P, P, U64, P, I, P]),
             "sbf_batch_query": (I, [P, P, U64, P, P, U64, P, U32P, U32P, I, P]),
@@ -410,6 +412,20 @@ class FilterServer:
 
     def reset_stats(self) -> None:
         _check(self._lib.sbf_server_reset_stats(self._h))
+
+
+def batch_query_noalloc(filters, seq, off, off_host, group, bits, hits, stream=None):
+    """Batched query whose scratch is a fixed array inside libsbf: for callers
+    that cannot allocate device memory.  ``bits`` and ``hits`` must be given
+    (preallocated int32 CUDA tensors); nothing is allocated here."""
+    lib = load_library()
+    arr = (ctypes.c_void_p * len(filters))(*[f.handle.value for f in filters])
+    oh = np.ascontiguousarray(off_host, dtype=np.uint64)
+    gr = np.ascontiguousarray(group, dtype=np.uint64)
+    _check(lib.sbf_batch_query_noalloc(arr, len(filters), _dev_ptr(seq, 1), seq.numel(),
+                                       _dev_ptr(off, 8), _host_ptr(oh), oh.size - 1, _host_ptr(gr),
+                                       _dev_ptr(bits, 4), _dev_ptr(hits, 4), _stream_handle(stream)))
+    return bits, hits
 
 
 def num_kmers(off: np.ndarray, k: int) -> int:
