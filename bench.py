@@ -552,6 +552,67 @@ def run_served(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# parameter sweep: s x m x H x shard bits x bits per k-mer on the 100 Mbp genome
+# ---------------------------------------------------------------------------
+def run_sweep(args):
+    import itertools
+
+    import torch
+
+    from paper_2606_24417_gb300 import build_lib, synth
+    from paper_2606_24417_gb300.sbf import SuperBloomFilter
+    from paper_2606_24417_gb300.stats import expected_fpr
+
+    build_lib.build()
+    torch.cuda.set_device(0)
+    genome = synth.bacterial_genome(GENOME_BP, seed=2)
+    n_s = n_r = 1_000_000
+    reads, roff = synth.mixed_query_reads(genome, n_s, n_r, READ_LEN, 0.01, seed=3)
+    dg = torch.from_numpy(genome).cuda()
+    dgo = torch.from_numpy(np.array([0, genome.size], dtype=np.int64)).cuda()
+    dq = torch.from_numpy(reads).cuda()
+    dqo = torch.from_numpy(roff.astype(np.int64)).cuda()
+    bits_out = torch.empty((reads.size + 31) // 32, dtype=torch.int32, device="cuda")
+    hits = torch.empty(n_s + n_r, dtype=torch.int32, device="cuda")
+    ins_kmers = genome.size - K + 1
+    q_kmers = (n_s + n_r) * (READ_LEN - K + 1)
+    rand_kmers = n_r * (READ_LEN - K + 1)
+    points = []
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for s, m, h, b, bpk in itertools.product((24, 26, 28, 31), (12, 14, 16, 20), (1, 2, 4, 8),
+                                             (256, 512), (8, 12, 16)):
+        f = SuperBloomFilter(K, m, s, h, bpk * ins_kmers, shard_bits=b)
+        f.insert(dg, dgo)   # warm (bits are idempotent)
+        f.query(dq, dqo, bits=bits_out, hits=hits)
+        e[0].record()
+        f.insert(dg, dgo)
+        e[1].record()
+        f.query(dq, dqo, bits=bits_out, hits=hits)
+        e[2].record()
+        torch.cuda.synchronize()
+        fp = int(hits[n_s:].sum().item())
+        words = f.words()
+        points.append({"s": s, "m": m, "H": h, "B": b, "bits_per_kmer": bpk, "fused": f.fused,
+                       "insert_ms": e[0].elapsed_time(e[1]), "query_ms": e[1].elapsed_time(e[2]),
+                       "insert_kmers_per_s": ins_kmers / (e[0].elapsed_time(e[1]) / 1e3),
+                       "query_kmers_per_s": q_kmers / (e[1].elapsed_time(e[2]) / 1e3),
+                       "fpr_measured": fp / rand_kmers, "fpr_expected": expected_fpr(words, K, s, h, b),
+                       "fill": float(np.bitwise_count(words).sum() / (words.size * 64))
+                       if hasattr(np, "bitwise_count") else None})
+        f.close()
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    with open(os.path.join(ROOT, "gpurun_out", "sweep.json"), "w") as fh:
+        json.dump(points, fh)
+    best = min((p for p in points if p["bits_per_kmer"] == 16), key=lambda p: p["fpr_measured"])
+    print(json.dumps({"workload": "sweep: 100 Mbp bacterial-shaped genome, s in {24,26,28,31}, "
+                      "m in {12,14,16,20}, H in {1,2,4,8}, shard bits {256,512}, 8/12/16 bits per "
+                      "k-mer; 1M sampled + 1M random 150 bp query reads (FPR from the random half)",
+                      "points": len(points), "lowest_fpr_at_16_bits": best,
+                      "written": "gpurun_out/sweep.json"}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -560,7 +621,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: 2M query reads (300 MB, still larger than L2) for profiling")
-    ap.add_argument("--workload", default="bacterial", choices=["bacterial", "batched", "served"],
+    ap.add_argument("--workload", default="bacterial", choices=["bacterial", "batched", "served", "sweep"],
                     help="batched: the many-filter workload (its own JSON line)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="device-timed steps only (no e2e, no CPU baseline): profiling runs")
@@ -577,6 +638,8 @@ def main():
         return run_batched(args) if rank == 0 else 0
     if args.workload == "served":
         return run_served(args) if rank == 0 else 0
+    if args.workload == "sweep":
+        return run_sweep(args) if rank == 0 else 0
     if world > 1:
         import torch
         import torch.distributed as dist
