@@ -31,7 +31,9 @@ def findere_fpr(eps: float, k: int, s: int) -> float:
 def sector_layout(H: int, shard_bits: int):
     """(S sectors, sector_bits, c_j counts) of the sectorised shard."""
     W = shard_bits // 64
-    S = min(H, W)
+    S = 1
+    while 2 * S <= min(H, W):   # largest power of two not above min(H, W)
+        S *= 2
     sector_bits = shard_bits // S
     c = np.array([sum(1 for i in range(H) if i % S == j) for j in range(S)], dtype=np.int64)
     return S, sector_bits, c

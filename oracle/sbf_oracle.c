@@ -27,8 +27,9 @@
  *   shard:     x = floor(mix64(mu ^ 0x14057B7EF767814F) * N / 2^64).
  *   s-mer:     h = mix64(v ^ 0x5851F42D4C957F2D) (the stronger mix, Sec. IV-G).
  *   layout:    shard x owns bits [x*B, (x+1)*B) of a little-endian array of
- *              64-bit words.  W = B/64 words, S = min(H, W) sectors of B/S
- *              bits; hash i uses sector i mod S (Sec. IV-B).
+ *              64-bit words.  W = B/64 words, S = the largest power of two
+ *              not above min(H, W) sectors of B/S bits; hash i uses sector
+ *              i mod S (Sec. IV-B: four equal sectors, hash i in sector i mod 4).
  *   bit:       b = log2(B/S), q = floor(64/H).  If q >= b, hash i takes bits
  *              [i*q, i*q+b) of h (bit-slicing); otherwise the top b bits of
  *              h * (0x9E3779B97F4A7C15 * (2i+1)) mod 2^64 (salted multiply,
@@ -125,9 +126,16 @@ static int log2_exact(int v) {
 }
 
 /* Bit index inside the shard for hash function i of s-mer hash h. */
+static int sector_count(int H, int W) {
+  int lim = H < W ? H : W;
+  int S = 1;
+  while (2 * S <= lim) S *= 2;
+  return S;
+}
+
 static uint64_t bit_in_shard(const oracle_sbf* f, uint64_t h, int i) {
   int W = f->B / 64;
-  int S = f->H < W ? f->H : W;
+  int S = sector_count(f->H, W);
   int sector_bits = f->B / S;
   int b = log2_exact(sector_bits);
   int q = 64 / f->H;

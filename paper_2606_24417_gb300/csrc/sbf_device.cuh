@@ -32,7 +32,7 @@ struct Geom {
   int k, m, s, H;
   int shard_bits;      // B
   int canonical;
-  int sectors;         // S = min(H, B/64)
+  int sectors;         // S = largest power of two <= min(H, B/64)
   int sector_bits;     // B / S
   int sector_log2;     // b = log2(B / S)
   int slice;           // q = floor(64 / H)
@@ -47,7 +47,9 @@ __host__ __device__ inline Geom make_geom(uint64_t* words, uint64_t n_shards, in
   g.shard_bits = shard_bits;
   g.canonical = canonical;
   int W = shard_bits / 64;
-  g.sectors = H < W ? H : W;
+  int lim = H < W ? H : W;  // sectors: the largest power of two not above min(H, W)
+  g.sectors = 1;
+  while (2 * g.sectors <= lim) g.sectors *= 2;
   g.sector_bits = shard_bits / g.sectors;
   int b = 0;
   while ((1 << b) < g.sector_bits) ++b;

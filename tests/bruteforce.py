@@ -61,7 +61,7 @@ class BruteSBF:
         """Absolute bit indices of canonical s-mer v in shard x."""
         h = mix64(v ^ 0x5851F42D4C957F2D)
         W = self.B // 64
-        S = min(self.H, W)
+        S = 1 << (min(self.H, W).bit_length() - 1)
         sector_bits = self.B // S
         b = sector_bits.bit_length() - 1
         q = 64 // self.H

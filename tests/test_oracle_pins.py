@@ -83,6 +83,8 @@ CONFIGS = [
     (31, 16, 28, 16, 1 << 16, 512, True),  # q = 4 < b: salted multiply
     (21, 11, 17, 12, 5000, 512, True),     # non power-of-two shard count
     (32, 16, 30, 4, 1 << 15, 512, True),   # k = 32
+    (31, 16, 28, 3, 1 << 15, 512, True),   # H = 3: two sectors
+    (31, 16, 28, 6, 1 << 15, 256, True),   # H = 6: four sectors, two slices share one
 ]
 
 
