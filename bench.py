@@ -46,6 +46,24 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def max_over_ranks(values, dist=None, device=None):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the
+    job's time).  Ranks are independent filter replicas working on their own
+    reads; this reduction of a few floats is the only cross-rank traffic."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def rank_read_seed(rank: int) -> int:
+    """Seed of a rank's query reads: every rank queries its own batch (weak scaling)."""
+    return 3 + 1000 * rank
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -115,7 +133,7 @@ def make_workload(rank: int, small: bool = False):
     genome = synth.bacterial_genome(GENOME_BP, seed=2)
     n_s, n_r = (N_SAMPLED // 10, N_RANDOM // 10) if small else (N_SAMPLED, N_RANDOM)
     reads, roff = synth.mixed_query_reads(genome, n_s, n_r, READ_LEN, 0.01,
-                                          seed=3 + 1000 * rank)
+                                          seed=rank_read_seed(rank))
     log(f"[bench] rank {rank}: workload generated in {time.time() - t:.1f}s")
     return genome, reads, roff
 
@@ -303,12 +321,7 @@ def run_ours(args, rank, world, local_rank):
     t_ins = [evs[i][0].elapsed_time(evs[i][1]) for i in range(args.steps)]
     t_q = [evs[i][1].elapsed_time(evs[i][2]) for i in range(args.steps)]
     total_ms = sum(t_ins) + sum(t_q)
-    if dist:
-        t = torch.tensor([total_ms, sum(t_ins), sum(t_q)], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, ins_ms_sum, q_ms_sum = t.tolist()
-    else:
-        ins_ms_sum, q_ms_sum = sum(t_ins), sum(t_q)
+    total_ms, ins_ms_sum, q_ms_sum = max_over_ranks([total_ms, sum(t_ins), sum(t_q)], dist, dev)
     value = world * kmers_step * args.steps / (total_ms / 1e3)
 
     if args.skip_extras:
@@ -339,10 +352,7 @@ def run_ours(args, rank, world, local_rank):
         f.query_host(h_reads, h_roff, h_bits, h_hits)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks([e2e_s], dist, dev)[0]
     # e2e answers equal the device-resident answers
     same = bool(np.array_equal(h_bits, d_bits.cpu().numpy().view(np.uint32)) and
                 np.array_equal(h_hits, d_hits.cpu().numpy().view(np.uint32)))
