@@ -57,6 +57,7 @@ cudaError_t launch_params(const Params& P, bool insert, cudaStream_t st) { retur
 bool fused_supported(const Geom& g) {
   if (getenv("SBF_FORCE_GENERIC")) return false;
   if (g.k < 2 || g.k > 32) return false;
+  if (g.s <= 16) return false;  // the s-mer extraction shifts by 64 - 2s < 32
   int w = fused::window_of(g);
   if (w != 12 && w != 16 && w != 18 && w != 20) return false;
   if ((2 * g.m > 32) != fused::key64_for(w)) return false;

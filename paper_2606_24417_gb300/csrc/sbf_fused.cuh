@@ -153,7 +153,7 @@ struct alignas(16) WarpSmem {
   uint32_t shard[kSlotCap * L::SLOT];    // shard copies (query) or masks (insert)
   SlotT slot_x[512];
   Pack hs[kLanePos * kHsStride];         // s-mer bit-address packs, [j][lane]
-  uint16_t slot_of[kLanePos * 34];       // slot of each valid position, [j][lane]
+  uint16_t end_slot[512];                // slot of each run end
   uint16_t end_list[512];                // run-end positions
   uint16_t slot_head[512];               // run-head position of each slot
   uint32_t fwd[kStage];                  // staged 2-bit words
@@ -278,7 +278,6 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
   constexpr int U = Shape<W>::kUseful;
   constexpr int ADV = Shape<W>::kAdvance;
   constexpr int HS = Sm::kHsStride;
-  constexpr int SO = 34;  // slot_of stride ([j][lane] layout)
   Geom g = P.g;
   g.words = seg.words;
   g.n_shards = seg.n_shards;
@@ -557,8 +556,11 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
           S.slot_x[sl] = (typename Sm::SlotT)mk[j];
           S.slot_head[sl] = (uint16_t)t;
         }
-        if ((valid16 >> j) & 1u) S.slot_of[j * SO + lane] = (uint16_t)sl;
-        if ((end16 >> j) & 1u) S.end_list[en++] = (uint16_t)t;
+        if ((end16 >> j) & 1u) {
+          S.end_list[en] = (uint16_t)t;
+          S.end_slot[en] = (uint16_t)sl;
+          ++en;
+        }
       }
     }
     reinterpret_cast<uint16_t*>(S.valid_w)[lane] = (uint16_t)valid16;
@@ -601,16 +603,35 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
     if constexpr (!INSERT) asm volatile("cp.async.commit_group;\n" ::);
 
     // ---------------- s-mer bit-address packs (overlaps the copies) -------
+    // s > 16 on this path, so the right shift 64 - 2s is below 32 and the
+    // 64-bit extraction is two funnel shifts.  mix64(v ^ K) starts with
+    // x ^= x >> 30, which is linear: (v ^ K) ^ ((v ^ K) >> 30) =
+    // v ^ (v >> 30) ^ K30 with the constant K30 = K ^ (K >> 30).
+    constexpr uint64_t K30 = kSmerKey ^ (kSmerKey >> 30);
+    const uint32_t sh_s = 64u - 2u * (uint32_t)s;
+    const uint32_t smask_hi = (uint32_t)(smask >> 32);
+    // 32-bit packs stay in registers for the own-pair tests; 64-bit packs
+    // (H = 8) are read back from shared memory to keep registers free
+    constexpr bool kPackRegs = sizeof(Pack) == 4;
+    Pack pk[kPackRegs ? kLanePos : 1];
 #pragma unroll
     for (int j = 0; j < kLanePos; ++j) {
       const uint32_t hi = __funnelshift_l(F1, F0, 2 * j);
       const uint32_t lo = __funnelshift_l(F2, F1, 2 * j);
       const uint32_t rlo = __funnelshift_r(R2, R1, 2 * j);
-      const uint32_t rhi = __funnelshift_r(R1, R0, 2 * j);
-      const uint64_t fs = (((uint64_t)hi << 32) | lo) >> (64 - 2 * s);
-      const uint64_t rs = (((uint64_t)rhi << 32) | rlo) & smask;
-      const uint64_t cs = (canon && rs < fs) ? rs : fs;
-      S.hs[j * HS + lane] = make_pack<H, B>(mix64(cs ^ kSmerKey));
+      const uint32_t rhi = __funnelshift_r(R1, R0, 2 * j) & smask_hi;
+      const uint32_t flo = __funnelshift_r(lo, hi, sh_s);
+      const uint32_t fhi = hi >> sh_s;
+      const bool use_rc = canon && (rhi < fhi || (rhi == fhi && rlo < flo));
+      const uint64_t cs = use_rc ? (((uint64_t)rhi << 32) | rlo) : (((uint64_t)fhi << 32) | flo);
+      uint64_t x = cs ^ (cs >> 30) ^ K30;
+      x *= kMixMul1;
+      x ^= x >> 27;
+      x *= kMixMul2;
+      x ^= x >> 31;
+      const Pack pj = make_pack<H, B>(x);
+      if constexpr (kPackRegs) pk[j] = pj;
+      S.hs[j * HS + lane] = pj;
     }
     if constexpr (!INSERT) asm volatile("cp.async.wait_group 0;\n" ::);
     __syncwarp();
@@ -655,29 +676,29 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
       }
     };
 
-    // own pairs (t, shard(t)), position-per-lane: t = 32*pass + lane, so
-    // t & 15 = lane & 15 and t >> 4 = 2*pass + (lane >> 4)
+    // own pairs (t, shard(t)), in the lane's own chunk: the packs are still in
+    // registers and the slot of position j is the lane's running slot count
     {
-      const uint32_t hs_i0 = (lane & 15u) * HS + (lane >> 4);
-      const uint32_t so_i0 = (lane & 15u) * SO + (lane >> 4);
-#pragma unroll 1
-      for (int pass = 0; pass < 16; ++pass) {
-        const bool v = (S.valid_w[pass] >> lane) & 1u;
-        bool ok = false;
-        if (v) {
-          const Pack pk = S.hs[hs_i0 + 2 * pass];
-          const uint32_t slot = S.slot_of[so_i0 + 2 * pass];
-          if constexpr (INSERT) {
-            set_pair(pk, slot);
+      uint32_t own16 = 0u;
+      uint32_t sl = slot_base - 1u;
+#pragma unroll
+      for (int j = 0; j < kLanePos; ++j) {
+        sl += (slot16 >> j) & 1u;
+        if ((valid16 >> j) & 1u) {
+          Pack pj;
+          if constexpr (kPackRegs) {
+            pj = pk[j];
           } else {
-            ok = test_pair(pk, slot);
+            pj = S.hs[j * HS + lane];
+          }
+          if constexpr (INSERT) {
+            set_pair(pj, sl);
+          } else {
+            own16 |= (uint32_t)test_pair(pj, sl) << j;
           }
         }
-        if constexpr (!INSERT) {
-          const unsigned own = __ballot_sync(kFull, ok);
-          if (lane == 0) S.own_w[pass] = own;
-        }
       }
+      if constexpr (!INSERT) reinterpret_cast<uint16_t*>(S.own_w)[lane] = (uint16_t)own16;
     }
 
     // extra pairs after each run end e: (e+d, shard(e)), d = 1..z.  A failure
@@ -685,7 +706,7 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
     // d gives the largest range, so testing stops there.
     for (uint32_t ei = lane; ei < total_ends; ei += 32) {
       const uint32_t e = S.end_list[ei];
-      const uint32_t slot = S.slot_of[(e & 15u) * SO + (e >> 4)];
+      const uint32_t slot = S.end_slot[ei];
       if constexpr (INSERT) {
         for (int d = 1; d <= z; ++d) {
           const uint32_t t = e + d;
