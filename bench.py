@@ -331,10 +331,13 @@ def run_ours(args, rank, world, local_rank):
         return 0
 
     # ---- e2e through the host entry points (pinned host buffers) ----------
-    h_genome = torch.from_numpy(genome).pin_memory().numpy()
-    h_goff = goff
-    h_reads = torch.from_numpy(reads).pin_memory().numpy()
-    h_roff = roff
+    def pinned(a):
+        return torch.from_numpy(np.ascontiguousarray(a).view(np.uint8)).pin_memory().numpy().view(a.dtype)
+
+    h_genome = pinned(genome)
+    h_goff = pinned(goff)
+    h_reads = pinned(reads)
+    h_roff = pinned(roff)
     h_bits = torch.empty((reads.size + 31) // 32, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
     h_hits = torch.empty(n_reads, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
     e2e_steps = max(1, min(args.steps, 3))

@@ -10,6 +10,7 @@
 #include <new>
 #include <vector>
 
+#include "sbf_fused.cuh"
 #include "sbf_internal.h"
 
 namespace sbf {
@@ -335,6 +336,91 @@ int ensure_host_buffers(sbf_filter* f, uint64_t seq_cap, uint64_t reads_cap) {
   return SBF_OK;
 }
 
+// Host path of filters with fused kernels.  A chunk's bytes are copied from
+// the 32-aligned position A <= off[r0], and the kernel takes the caller's
+// offsets unchanged: its sequence and answer pointers are shifted back by A
+// so that absolute positions index the chunk buffers (the kernel only reads
+// positions >= A).  No offset is rewritten on the host.
+int host_run_fused(sbf_filter* f, bool is_query, const uint8_t* h_seq, const uint64_t* h_off,
+                   uint64_t n_reads, uint32_t* h_bits, uint32_t* h_hits) {
+  std::vector<Chunk> chunks = plan_chunks(h_off, n_reads, true);
+  uint64_t seq_cap = 0, reads_cap = 0;
+  for (const Chunk& c : chunks) {
+    seq_cap = std::max(seq_cap, c.end - c.a);
+    reads_cap = std::max(reads_cap, c.r1 - c.r0);
+  }
+  std::lock_guard<std::mutex> lock(f->host_mu);
+  DeviceGuard dg(f->device);
+  int rc = ensure_host_buffers(f, seq_cap, reads_cap);
+  if (rc != SBF_OK) return rc;
+  const uint64_t adv = (uint64_t)fused::advance_of(f->geom);
+  std::vector<uint32_t> first_words(chunks.size(), 0);
+  for (size_t ci = 0; ci < chunks.size(); ++ci) {
+    const Chunk& c = chunks[ci];
+    const int b = (int)(ci & 1);
+    cudaStream_t st = f->host_streams[b];
+    cudaError_t e = cudaStreamSynchronize(st);  // buffer set b is free again
+    if (e != cudaSuccess) return cuda_fail(e, "host path sync");
+    const uint64_t len = c.end - c.a, nr = c.r1 - c.r0, nwords = (len + 31) / 32;
+    if ((e = cudaMemcpyAsync(f->host_dev_seq[b], h_seq + c.a, len, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(f->host_dev_off[b], h_off + c.r0, (nr + 1) * 8, cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess)
+      return cuda_fail(e, "host path H2D");
+    const bool want_bits = is_query && h_bits;
+    const bool want_hits = is_query && h_hits;
+    if (want_bits && (e = cudaMemsetAsync(f->host_dev_bits[b], 0, nwords * 4, st)) != cudaSuccess)
+      return cuda_fail(e, "memset");
+    if (want_hits && (e = cudaMemsetAsync(f->host_dev_hits[b], 0, nr * 4, st)) != cudaSuccess)
+      return cuda_fail(e, "memset");
+    fused::Params P{};
+    P.g = f->geom;
+    P.seq = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(f->host_dev_seq[b]) - c.a);
+    P.seq_len = c.end;
+    P.bits = want_bits ? reinterpret_cast<uint32_t*>(reinterpret_cast<uintptr_t>(f->host_dev_bits[b]) -
+                                                      (c.a / 32) * 4)
+                       : nullptr;
+    P.stats = nullptr;
+    P.segs = nullptr;
+    P.n_segs = 1;
+    P.seg0 = fused::Segment{f->geom.words, f->geom.n_shards, f->host_dev_off[b], nr,
+                            want_hits ? f->host_dev_hits[b] : nullptr, c.a, 0, (len + adv - 1) / adv};
+    P.iters = P.seg0.iters;
+    P.work = nullptr;
+    P.chunk = 1;
+    P.grid_blocks = 0;
+    if ((e = fused::launch_params(P, !is_query, st)) != cudaSuccess) return cuda_fail(e, "host path launch");
+    if (want_hits &&
+        (e = cudaMemcpyAsync(h_hits + c.r0, f->host_dev_hits[b], nr * 4, cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess)
+      return cuda_fail(e, "host path D2H");
+    if (want_bits) {
+      if (nwords > 1 && (e = cudaMemcpyAsync(h_bits + c.a / 32 + 1, f->host_dev_bits[b] + 1,
+                                             (nwords - 1) * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "host path D2H");
+      if ((e = cudaMemcpyAsync(&first_words[ci], f->host_dev_bits[b], 4, cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess)
+        return cuda_fail(e, "host path D2H");
+    }
+  }
+  for (int b = 0; b < 2; ++b) {
+    cudaError_t e = cudaStreamSynchronize(f->host_streams[b]);
+    if (e != cudaSuccess) return cuda_fail(e, "host path sync");
+  }
+  if (is_query && h_bits) {
+    // word A/32 of a chunk: its bits below off[r0] belong to the previous chunk
+    for (size_t ci = 0; ci < chunks.size(); ++ci) {
+      const Chunk& c = chunks[ci];
+      const uint64_t lead = h_off[c.r0] - c.a;
+      const uint32_t mine = first_words[ci] & (lead >= 32 ? 0u : (~0u << lead));
+      const uint64_t w0 = c.a / 32;
+      const uint32_t prev = (ci > 0 && chunks[ci - 1].end > c.a) ? h_bits[w0] : 0u;
+      h_bits[w0] = prev | mine;
+    }
+  }
+  return SBF_OK;
+}
+
 int host_run(sbf_filter* f, bool is_query, const uint8_t* h_seq, uint64_t seq_len,
              const uint64_t* h_off, uint64_t n_reads, uint32_t* h_bits, uint32_t* h_hits) {
   if (n_reads == 0) {
@@ -346,6 +432,7 @@ int host_run(sbf_filter* f, bool is_query, const uint8_t* h_seq, uint64_t seq_le
       return fail(SBF_EINVAL, "offsets decrease at read %llu", (unsigned long long)r);
   if (h_off[0] != 0 || h_off[n_reads] != seq_len)
     return fail(SBF_EINVAL, "offsets must start at 0 and end at seq_len");
+  if (f->fused) return host_run_fused(f, is_query, h_seq, h_off, n_reads, h_bits, h_hits);
   const uint64_t dummy = is_query ? 1 : 0;  // leading dummy read of query chunks
   std::vector<Chunk> chunks = plan_chunks(h_off, n_reads, is_query);
   uint64_t seq_cap = 0, reads_cap = 0;

@@ -116,6 +116,62 @@ __device__ __forceinline__ uint32_t pack_addr(typename Layout<H, B>::Pack pk, in
 
 // One filter's share of a launch: the filter, the reads it serves (a slice
 // of the offset table, absolute positions) and the positions to cover.
+// Shared-memory bit test / set of one s-mer's H addresses in a shard slot.
+// The byte offset of hash i's 32-bit word inside its sector is
+// ((p_i >> 5) << 2) = (p_i >> 3) & ~3, masked to the sector: one shift and
+// mask yield it for all packed bytes at once, a byte permute picks one.  The
+// funnel shift uses only the low 5 bits of its amount, so p_i itself (the
+// pack shifted to byte i) serves as the bit index.
+template <int H, int B>
+__device__ __forceinline__ uint32_t test_slot(const uint32_t* slot_words,
+                                              typename Layout<H, B>::Pack pk) {
+  using L = Layout<H, B>;
+  constexpr uint32_t SBY = L::SB / 8;          // sector bytes
+  constexpr uint32_t OM = (SBY - 1u) & ~3u;   // word byte-offset mask
+  const char* base = reinterpret_cast<const char*>(slot_words);
+  uint32_t acc = 1u;
+  if constexpr (H == 1) {
+    const uint32_t p = (uint32_t)pk;
+    const uint32_t w = *reinterpret_cast<const uint32_t*>(base + ((p >> 3) & OM));
+    acc &= __funnelshift_r(w, w, p);
+  } else if constexpr (H <= 4) {
+    const uint32_t v = ((uint32_t)pk >> 3) & (OM * 0x01010101u);
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      const uint32_t off = __byte_perm(v, 0u, 0x4440u | (uint32_t)i);
+      const uint32_t sh = i == 0 ? (uint32_t)pk : __byte_perm((uint32_t)pk, 0u, 0x4440u | (uint32_t)i);
+      const uint32_t w = *reinterpret_cast<const uint32_t*>(base + (i % L::S) * SBY + off);
+      acc &= __funnelshift_r(w, w, sh);
+    }
+  } else {
+    const uint32_t lo = (uint32_t)pk, hi = (uint32_t)(pk >> 32);
+    const uint32_t vlo = (lo >> 3) & (OM * 0x01010101u), vhi = (hi >> 3) & (OM * 0x01010101u);
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      const uint32_t src = i < 4 ? vlo : vhi;
+      const uint32_t srp = i < 4 ? lo : hi;
+      const uint32_t off = __byte_perm(src, 0u, 0x4440u | (uint32_t)(i & 3));
+      const uint32_t sh = __byte_perm(srp, 0u, 0x4440u | (uint32_t)(i & 3));
+      const uint32_t w = *reinterpret_cast<const uint32_t*>(base + (i % L::S) * SBY + off);
+      acc &= __funnelshift_r(w, w, sh);
+    }
+  }
+  return acc & 1u;
+}
+
+template <int H, int B>
+__device__ __forceinline__ void set_slot(uint32_t* slot_words, typename Layout<H, B>::Pack pk) {
+  using L = Layout<H, B>;
+  constexpr uint32_t SBY = L::SB / 8;
+  constexpr uint32_t OM = (SBY - 1u) & ~3u;
+  char* base = reinterpret_cast<char*>(slot_words);
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    const uint32_t p = pack_addr<H, B>(pk, i);
+    atomicOr(reinterpret_cast<uint32_t*>(base + (i % L::S) * SBY + ((p >> 3) & OM)), 1u << (p & 31u));
+  }
+}
+
 struct Segment {
   uint64_t* words;        // the filter's bit array
   uint64_t n_shards;
@@ -154,6 +210,7 @@ struct alignas(16) WarpSmem {
   SlotT slot_x[512];
   Pack hs[kLanePos * kHsStride];         // s-mer bit-address packs, [j][lane]
   uint16_t end_slot[512];                // slot of each run end
+  uint16_t slot_of[kLanePos * 34];       // slot of each valid position, [j][lane]
   uint16_t end_list[512];                // run-end positions
   uint16_t slot_head[512];               // run-head position of each slot
   uint32_t fwd[kStage];                  // staged 2-bit words
@@ -556,6 +613,7 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
           S.slot_x[sl] = (typename Sm::SlotT)mk[j];
           S.slot_head[sl] = (uint16_t)t;
         }
+        if ((valid16 >> j) & 1u) S.slot_of[j * 34 + lane] = (uint16_t)sl;
         if ((end16 >> j) & 1u) {
           S.end_list[en] = (uint16_t)t;
           S.end_slot[en] = (uint16_t)sl;
@@ -610,11 +668,8 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
     constexpr uint64_t K30 = kSmerKey ^ (kSmerKey >> 30);
     const uint32_t sh_s = 64u - 2u * (uint32_t)s;
     const uint32_t smask_hi = (uint32_t)(smask >> 32);
-    // 32-bit packs stay in registers for the own-pair tests; 64-bit packs
-    // (H = 8) are read back from shared memory to keep registers free
-    constexpr bool kPackRegs = sizeof(Pack) == 4;
-    Pack pk[kPackRegs ? kLanePos : 1];
-#pragma unroll
+    constexpr int kHashUnroll = KEY64 ? kLanePos : 2;  // small code where registers allow
+#pragma unroll kHashUnroll
     for (int j = 0; j < kLanePos; ++j) {
       const uint32_t hi = __funnelshift_l(F1, F0, 2 * j);
       const uint32_t lo = __funnelshift_l(F2, F1, 2 * j);
@@ -629,43 +684,27 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
       x ^= x >> 27;
       x *= kMixMul2;
       x ^= x >> 31;
-      const Pack pj = make_pack<H, B>(x);
-      if constexpr (kPackRegs) pk[j] = pj;
-      S.hs[j * HS + lane] = pj;
+      S.hs[j * HS + lane] = make_pack<H, B>(x);
     }
     if constexpr (!INSERT) asm volatile("cp.async.wait_group 0;\n" ::);
     __syncwarp();
 
     // ---------------- pair tests / sets ------------------------------------
     auto test_pair = [&](Pack pk, uint32_t slot) -> bool {
+      if (slot < (uint32_t)kSlotCap) return test_slot<H, B>(&S.shard[slot * L::SLOT], pk) != 0u;
       uint32_t acc = 1u;
-      if (slot < (uint32_t)kSlotCap) {
-        const uint32_t* sp = &S.shard[slot * L::SLOT];
+      const uint32_t* gp = words32 + S.slot_x[slot] * (uint64_t)L::W32;
 #pragma unroll
-        for (int i = 0; i < H; ++i) {
-          const uint32_t p = pack_addr<H, B>(pk, i);
-          const uint32_t w = sp[(i % L::S) * L::SW32 + (p >> 5)];
-          acc &= __funnelshift_r(w, w, p);
-        }
-      } else {
-        const uint32_t* gp = words32 + S.slot_x[slot] * (uint64_t)L::W32;
-#pragma unroll
-        for (int i = 0; i < H; ++i) {
-          const uint32_t p = pack_addr<H, B>(pk, i);
-          const uint32_t w = __ldg(gp + (i % L::S) * L::SW32 + (p >> 5));
-          acc &= __funnelshift_r(w, w, p);
-        }
+      for (int i = 0; i < H; ++i) {
+        const uint32_t p = pack_addr<H, B>(pk, i);
+        const uint32_t w = __ldg(gp + (i % L::S) * L::SW32 + (p >> 5));
+        acc &= __funnelshift_r(w, w, p);
       }
       return acc & 1u;
     };
     auto set_pair = [&](Pack pk, uint32_t slot) {
       if (slot < (uint32_t)kSlotCap) {
-        uint32_t* sp = &S.shard[slot * L::SLOT];
-#pragma unroll
-        for (int i = 0; i < H; ++i) {
-          const uint32_t p = pack_addr<H, B>(pk, i);
-          atomicOr(&sp[(i % L::S) * L::SW32 + (p >> 5)], 1u << (p & 31u));
-        }
+        set_slot<H, B>(&S.shard[slot * L::SLOT], pk);
       } else {
         uint32_t* gp = words32 + S.slot_x[slot] * (uint64_t)L::W32;
 #pragma unroll
@@ -676,29 +715,36 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
       }
     };
 
-    // own pairs (t, shard(t)), in the lane's own chunk: the packs are still in
-    // registers and the slot of position j is the lane's running slot count
+    // own pairs (t, shard(t)), position-per-lane: t = 32*pass + lane, so
+    // t & 15 = lane & 15 and t >> 4 = 2*pass + (lane >> 4); lanes of one pass
+    // mostly share a few run slots, so their shard reads broadcast.  Two
+    // passes per step for independent work; invalid positions test slot 0
+    // (their slot entry may be stale) and are masked out.
     {
-      uint32_t own16 = 0u;
-      uint32_t sl = slot_base - 1u;
-#pragma unroll
-      for (int j = 0; j < kLanePos; ++j) {
-        sl += (slot16 >> j) & 1u;
-        if ((valid16 >> j) & 1u) {
-          Pack pj;
-          if constexpr (kPackRegs) {
-            pj = pk[j];
-          } else {
-            pj = S.hs[j * HS + lane];
-          }
-          if constexpr (INSERT) {
-            set_pair(pj, sl);
-          } else {
-            own16 |= (uint32_t)test_pair(pj, sl) << j;
+      const uint32_t hs_i0 = (lane & 15u) * HS + (lane >> 4);
+      const uint32_t so_i0 = (lane & 15u) * 34 + (lane >> 4);
+#pragma unroll 1
+      for (int pass = 0; pass < 16; pass += 2) {
+        const uint32_t va = (S.valid_w[pass] >> lane) & 1u;
+        const uint32_t vb = (S.valid_w[pass + 1] >> lane) & 1u;
+        const Pack pka = S.hs[hs_i0 + 2 * pass];
+        const Pack pkb = S.hs[hs_i0 + 2 * pass + 2];
+        const uint32_t sla = va ? (uint32_t)S.slot_of[so_i0 + 2 * pass] : 0u;
+        const uint32_t slb = vb ? (uint32_t)S.slot_of[so_i0 + 2 * pass + 2] : 0u;
+        if constexpr (INSERT) {
+          if (va) set_pair(pka, sla);
+          if (vb) set_pair(pkb, slb);
+        } else {
+          const bool oka = ((uint32_t)test_pair(pka, sla) & va) != 0u;
+          const bool okb = ((uint32_t)test_pair(pkb, slb) & vb) != 0u;
+          const unsigned own_a = __ballot_sync(kFull, oka);
+          const unsigned own_b = __ballot_sync(kFull, okb);
+          if (lane == 0) {
+            S.own_w[pass] = own_a;
+            S.own_w[pass + 1] = own_b;
           }
         }
       }
-      if constexpr (!INSERT) reinterpret_cast<uint16_t*>(S.own_w)[lane] = (uint16_t)own16;
     }
 
     // extra pairs after each run end e: (e+d, shard(e)), d = 1..z.  A failure

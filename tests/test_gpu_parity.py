@@ -190,12 +190,15 @@ def test_insert_order_and_repeats_on_gpu():
                        np.array([0, rep.size], np.uint64))
 
 
-def test_host_path_matches_device(monkeypatch):
-    params = (31, 16, 28, 4, 1 << 22, 512, True)
+@pytest.mark.parametrize("params", [(31, 16, 28, 4, 1 << 22, 512, True),   # fused kernels
+                                    (9, 5, 6, 2, 1 << 18, 256, True)],     # generic kernels
+                         ids=["fused", "generic"])
+def test_host_path_matches_device(monkeypatch, params):
     ins_seq, ins_off = ragged_reads(4000, 31)
     q_seq, q_off = ragged_reads(6000, 32)
     monkeypatch.setenv("SBF_HOST_CHUNK_BYTES", "40000")   # many chunk seams
     f = make_filter(*params[:5], params[5], params[6])
+    assert f.fused == (params[0] == 31)
     f.insert_host(ins_seq, ins_off)
     o = OracleSBF(*params[:5], shard_bits=params[5])
     o.insert(ins_seq, ins_off)
