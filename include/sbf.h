@@ -19,9 +19,11 @@
  *  - A batch of reads is one concatenated byte array `seq` of `seq_len` bytes
  *    and `n_reads + 1` offsets: read r is seq[off[r], off[r+1]).  Offsets are
  *    non-decreasing, off[0] = 0 and off[n_reads] = seq_len.  K-mers never
- *    span two reads.  Calls with device offsets cannot check them without a
- *    synchronisation: offsets outside [0, seq_len] are clamped, so a
- *    malformed table gives wrong answers but no out-of-bounds access.
+ *    span two reads.  Offsets are not checked one by one (on the device that
+ *    would need a synchronisation, on the host a pass over all reads); only
+ *    the first and last (and group boundaries) are.  Offsets outside
+ *    [0, seq_len] are clamped, so a malformed table gives wrong answers but
+ *    no out-of-bounds access.
  *  - Query answers are bit-packed by START POSITION in `seq` (as Alg. 2
  *    writes output[blockStartKmer + localIdx]): bit p of a uint32 array
  *    (word p >> 5, bit p & 31) is 1 iff a valid k-mer starts at p and is

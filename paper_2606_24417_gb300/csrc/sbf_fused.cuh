@@ -668,7 +668,7 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
     constexpr uint64_t K30 = kSmerKey ^ (kSmerKey >> 30);
     const uint32_t sh_s = 64u - 2u * (uint32_t)s;
     const uint32_t smask_hi = (uint32_t)(smask >> 32);
-    constexpr int kHashUnroll = KEY64 ? kLanePos : 2;  // small code where registers allow
+    constexpr int kHashUnroll = KEY64 ? kLanePos : 4;  // small code where registers allow
 #pragma unroll kHashUnroll
     for (int j = 0; j < kLanePos; ++j) {
       const uint32_t hi = __funnelshift_l(F1, F0, 2 * j);

@@ -92,11 +92,9 @@ extern "C" int sbf_batch_query_noalloc(sbf_filter* const* filters, int n_filters
     return fail(SBF_EINVAL, "offsets must start at 0 and end at seq_len");
   if (h_group[0] != 0 || h_group[n_filters] != n_reads)
     return fail(SBF_EINVAL, "groups must start at read 0 and end at n_reads");
-  for (uint64_t r = 0; r < n_reads; ++r)
-    if (h_off[r + 1] < h_off[r])
-      return fail(SBF_EINVAL, "offsets decrease at read %llu", (unsigned long long)r);
   for (int i = 0; i < n_filters; ++i)
-    if (h_group[i + 1] < h_group[i]) return fail(SBF_EINVAL, "groups decrease at filter %d", i);
+    if (h_group[i + 1] < h_group[i] || h_off[h_group[i + 1]] < h_off[h_group[i]])
+      return fail(SBF_EINVAL, "groups or offsets decrease at filter %d", i);
 
   DeviceGuard dg(f0->device);
   unsigned char* scratch = nullptr;
