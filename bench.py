@@ -513,7 +513,9 @@ def run_served(args):
     for i, sz in enumerate(sizes):
         n = max(1, int(sz) // READ_LEN)
         seq, off = synth.sample_reads(genome, n, READ_LEN, 0.01, seed=5000 + i)
-        pool.append((torch.from_numpy(seq).pin_memory().numpy(), off, n * (READ_LEN - K + 1)))
+        pool.append((torch.from_numpy(seq).pin_memory().numpy(),
+                     torch.from_numpy(off.view(np.int64)).pin_memory().numpy().view(np.uint64),
+                     n * (READ_LEN - K + 1)))
     mean_kmers = float(np.mean([p[2] for p in pool]))
     log(f"[bench] {n_pool} requests, {sum(p[0].size for p in pool) / 1e6:.0f} Mbp, "
         f"mean {mean_kmers / 1e3:.0f}k k-mers")

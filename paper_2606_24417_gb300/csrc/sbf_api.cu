@@ -158,6 +158,7 @@ void sbf_destroy(sbf_filter* f) {
     cudaFree(f->host_dev_hits[i]);
   }
   cudaFree(f->geom.words);
+  cudaFreeHost(f->host_first);
   delete f;
 }
 
@@ -299,6 +300,21 @@ std::vector<Chunk> plan_chunks(const uint64_t* off, uint64_t n_reads, bool align
   return out;
 }
 
+uint32_t* ensure_first_words(sbf_filter* f, uint64_t n) {
+  if (n > f->host_first_cap) {
+    cudaFreeHost(f->host_first);
+    f->host_first = nullptr;
+    f->host_first_cap = 0;
+    uint64_t cap = n < 64 ? 64 : n;
+    if (cudaMallocHost(&f->host_first, cap * sizeof(uint32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    f->host_first_cap = cap;
+  }
+  return f->host_first;
+}
+
 int ensure_host_buffers(sbf_filter* f, uint64_t seq_cap, uint64_t reads_cap) {
   for (int i = 0; i < 2; ++i) {
     if (!f->host_streams[i]) {
@@ -357,7 +373,8 @@ int host_run_fused(sbf_filter* f, bool is_query, const uint8_t* h_seq, const uin
   int rc = ensure_host_buffers(f, seq_cap, reads_cap);
   if (rc != SBF_OK) return rc;
   const uint64_t adv = (uint64_t)fused::advance_of(f->geom);
-  std::vector<uint32_t> first_words(chunks.size(), 0);
+  uint32_t* first_words = ensure_first_words(f, chunks.size());
+  if (!first_words) return fail(SBF_ENOMEM, "pinned host allocation failed");
   for (size_t ci = 0; ci < chunks.size(); ++ci) {
     const Chunk& c = chunks[ci];
     const int b = (int)(ci & 1);
@@ -378,16 +395,23 @@ int host_run_fused(sbf_filter* f, bool is_query, const uint8_t* h_seq, const uin
       return cuda_fail(e, "memset");
     fused::Params P{};
     P.g = f->geom;
-    P.seq = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(f->host_dev_seq[b]) - c.a);
-    P.seq_len = c.end;
-    P.bits = want_bits ? reinterpret_cast<uint32_t*>(reinterpret_cast<uintptr_t>(f->host_dev_bits[b]) -
-                                                      (c.a / 32) * 4)
-                       : nullptr;
     P.stats = nullptr;
     P.segs = nullptr;
     P.n_segs = 1;
-    P.seg0 = fused::Segment{f->geom.words, f->geom.n_shards, f->host_dev_off[b], nr,
-                            want_hits ? f->host_dev_hits[b] : nullptr, c.a, 0, (len + adv - 1) / adv};
+    fused::Segment& sg = P.seg0;
+    sg.words = f->geom.words;
+    sg.n_shards = f->geom.n_shards;
+    sg.seq = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(f->host_dev_seq[b]) - c.a);
+    sg.seq_len = c.end;
+    sg.off = f->host_dev_off[b];
+    sg.n_reads = nr;
+    sg.bits = want_bits ? reinterpret_cast<uint32_t*>(reinterpret_cast<uintptr_t>(f->host_dev_bits[b]) -
+                                                       (c.a / 32) * 4)
+                        : nullptr;
+    sg.hits = want_hits ? f->host_dev_hits[b] : nullptr;
+    sg.p_begin = c.a;
+    sg.iter_begin = 0;
+    sg.iters = (len + adv - 1) / adv;
     P.iters = P.seg0.iters;
     P.work = nullptr;
     P.chunk = 1;
@@ -448,7 +472,8 @@ int host_run(sbf_filter* f, bool is_query, const uint8_t* h_seq, uint64_t seq_le
   int rc = ensure_host_buffers(f, seq_cap, reads_cap);
   if (rc != SBF_OK) return rc;
   std::vector<uint64_t> offs[2];
-  std::vector<uint32_t> first_words(chunks.size(), 0);
+  uint32_t* first_words = ensure_first_words(f, chunks.size());
+  if (!first_words) return fail(SBF_ENOMEM, "pinned host allocation failed");
   for (size_t ci = 0; ci < chunks.size(); ++ci) {
     const Chunk& c = chunks[ci];
     int b = (int)(ci & 1);

@@ -76,9 +76,9 @@ struct DeviceGuard {
 };
 
 // Segment table of one call: filter f serves reads [group[f], group[f+1]).
-int build_table(const sbf_batch* b, const uint64_t* d_off, const uint64_t* h_off, uint64_t n_reads,
-                const uint64_t* h_group, uint32_t* d_hits, std::vector<Segment>& out,
-                uint64_t& total_iters) {
+int build_table(const sbf_batch* b, const uint8_t* d_seq, uint64_t seq_len, const uint64_t* d_off,
+                const uint64_t* h_off, uint64_t n_reads, const uint64_t* h_group, uint32_t* d_bits,
+                uint32_t* d_hits, std::vector<Segment>& out, uint64_t& total_iters) {
   const size_t nf = b->filters.size();
   if (h_group[0] != 0 || h_group[nf] != n_reads)
     return fail(SBF_EINVAL, "groups must start at read 0 and end at n_reads");
@@ -94,8 +94,11 @@ int build_table(const sbf_batch* b, const uint64_t* d_off, const uint64_t* h_off
     Segment s{};
     s.words = b->filters[f]->geom.words;
     s.n_shards = b->filters[f]->geom.n_shards;
+    s.seq = d_seq;
+    s.seq_len = seq_len;
     s.off = d_off + g0;
     s.n_reads = g1 - g0;
+    s.bits = d_bits;
     s.hits = d_hits ? d_hits + g0 : nullptr;
     s.iter_begin = it;
     if (g1 > g0) {
@@ -168,9 +171,6 @@ cudaError_t enqueue_fused(sbf_batch* b, bool insert, const uint8_t* seq, uint64_
     return e;
   Params P{};
   P.g = b->geom;
-  P.seq = seq;
-  P.seq_len = seq_len;
-  P.bits = insert ? nullptr : bits;
   P.stats = nullptr;
   P.segs = b->d_segs;
   P.n_segs = n_segs;
@@ -192,7 +192,8 @@ int run_batch(sbf_batch* b, bool insert, const uint8_t* d_seq, uint64_t seq_len,
   DeviceGuard dg(b->device);
   std::vector<Segment> table;
   uint64_t iters = 0;
-  int rc = build_table(b, d_off, h_off, n_reads, h_group, insert ? nullptr : d_hits, table, iters);
+  int rc = build_table(b, d_seq, seq_len, d_off, h_off, n_reads, h_group, insert ? nullptr : d_bits,
+                       insert ? nullptr : d_hits, table, iters);
   if (rc != SBF_OK) return rc;
   cudaError_t e;
   if (mode == SBF_BATCH_PER_FILTER) {
@@ -206,9 +207,6 @@ int run_batch(sbf_batch* b, bool insert, const uint8_t* d_seq, uint64_t seq_len,
       if (s.iters == 0) continue;
       Params P{};
       P.g = b->geom;
-      P.seq = d_seq;
-      P.seq_len = seq_len;
-      P.bits = insert ? nullptr : d_bits;
       P.segs = nullptr;
       P.n_segs = 1;
       P.seg0 = s;

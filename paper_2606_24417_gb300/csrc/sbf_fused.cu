@@ -35,14 +35,12 @@ static Params single(const Geom& g, const uint8_t* seq, uint64_t seq_len, const 
                      uint64_t n_reads, uint32_t* bits, uint32_t* hits, uint64_t* stats) {
   Params P{};
   P.g = g;
-  P.seq = seq;
-  P.seq_len = seq_len;
-  P.bits = bits;
   P.stats = stats;
   P.segs = nullptr;
   P.n_segs = 1;
   const uint64_t adv = (uint64_t)advance_of(g);
-  P.seg0 = Segment{g.words, g.n_shards, off, n_reads, hits, 0, 0, (seq_len + adv - 1) / adv};
+  P.seg0 = Segment{g.words, g.n_shards, seq,  seq_len, off, n_reads, bits, hits,
+                   0,       0,          (seq_len + adv - 1) / adv};
   P.iters = P.seg0.iters;
   P.work = nullptr;
   P.chunk = 1;

@@ -172,11 +172,17 @@ __device__ __forceinline__ void set_slot(uint32_t* slot_words, typename Layout<H
   }
 }
 
+// One share of a launch: a filter, the bytes and reads it serves and where
+// its answers go.  Positions are relative to `seq`; the offsets use the same
+// positions.
 struct Segment {
   uint64_t* words;        // the filter's bit array
   uint64_t n_shards;
-  const uint64_t* off;    // n_reads + 1 offsets (absolute positions in seq)
+  const uint8_t* seq;     // bytes; positions index this pointer
+  uint64_t seq_len;       // positions >= seq_len read as invalid bytes
+  const uint64_t* off;    // n_reads + 1 offsets (positions in seq)
   uint64_t n_reads;
+  uint32_t* bits;         // query: answer words indexed by position >> 5 (zeroed), or NULL
   uint32_t* hits;         // query: counts of these reads (zeroed by the launcher), or NULL
   uint64_t p_begin;       // first position covered (multiple of 16)
   uint64_t iter_begin;    // index of the segment's first iteration in the launch
@@ -185,9 +191,6 @@ struct Segment {
 
 struct Params {
   Geom g;                 // shared k, m, s, H, shard bits, canonical
-  const uint8_t* seq;
-  uint64_t seq_len;
-  uint32_t* bits;         // query: bit-packed answers (zeroed by the launcher), or NULL
   uint64_t* stats;        // query: valid k-mers, runs, positives, or NULL
   const Segment* segs;    // NULL: the launch is the single segment seg0
   uint32_t n_segs;
@@ -341,7 +344,7 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
   const int k = g.k, m = g.m, s = g.s, z = g.k - g.s;
   const bool canon = g.canonical != 0;
 
-  const uint64_t seq_len = P.seq_len;
+  const uint64_t seq_len = seg.seq_len;
   const uint64_t* off = seg.off;
   const uint64_t n_reads = seg.n_reads;
   // start positions outside [lo_pos, hi_pos) belong to no read
@@ -350,7 +353,7 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
     lo_pos = off[0] < seq_len ? off[0] : seq_len;
     hi_pos = off[n_reads] < seq_len ? off[n_reads] : seq_len;
   }
-  const bool aligned = (reinterpret_cast<uintptr_t>(P.seq) & 15u) == 0;
+  const bool aligned = (reinterpret_cast<uintptr_t>(seg.seq) & 15u) == 0;
   const uint64_t smask = (s >= 32) ? ~0ull : ((1ull << (2 * s)) - 1ull);
   const uint64_t mmask = (m >= 32) ? ~0ull : ((1ull << (2 * m)) - 1ull);
   uint32_t* words32 = reinterpret_cast<uint32_t*>(g.words);
@@ -368,9 +371,9 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
   if (n_reads > 0) r_cur_start = off[r_cur] < seq_len ? off[r_cur] : seq_len;
   uint64_t e_batch = read_end(r_cur + lane);              // prefetched first batch of read ends
   // prefetched raw bytes of the first iteration
-  uint4 raw_a = load16(P.seq, p0 + 16ull * lane, seq_len, aligned);
+  uint4 raw_a = load16(seg.seq, p0 + 16ull * lane, seq_len, aligned);
   uint4 raw_b = make_uint4(0, 0, 0, 0);
-  if (lane < kStage - 32) raw_b = load16(P.seq, p0 + 16ull * (lane + 32), seq_len, aligned);
+  if (lane < kStage - 32) raw_b = load16(seg.seq, p0 + 16ull * (lane + 32), seq_len, aligned);
 
   // run-head carry: validity and minimizer key of position p0 - 1
   bool carry_valid = false;
@@ -378,7 +381,7 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
   if (!INSERT && P.stats && p0 > 0) {
     KeyT kk = 0;
     bool v = false;
-    if (lane == 0) v = prev_kmer_key<KeyT>(g, P.seq, seq_len, off, n_reads, p0 - 1, kk);
+    if (lane == 0) v = prev_kmer_key<KeyT>(g, seg.seq, seq_len, off, n_reads, p0 - 1, kk);
     carry_valid = __shfl_sync(kFull, v, 0);
     if constexpr (KEY64) {
       carry_key = ((uint64_t)__shfl_sync(kFull, (uint32_t)(kk >> 32), 0) << 32) |
@@ -413,8 +416,8 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
       // prefetch the next iteration's bytes; they arrive while this one runs
       if (it + 1 < it1) {
         const uint64_t np = p0 + ADV;
-        raw_a = load16(P.seq, np + 16ull * lane, seq_len, aligned);
-        if (lane < kStage - 32) raw_b = load16(P.seq, np + 16ull * (lane + 32), seq_len, aligned);
+        raw_a = load16(seg.seq, np + 16ull * lane, seq_len, aligned);
+        if (lane < kStage - 32) raw_b = load16(seg.seq, np + 16ull * (lane + 32), seq_len, aligned);
       }
     }
     if (lane < 17) {
@@ -810,16 +813,16 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
         S.k_w[lane] = K;
         if (P.stats) st_pos += __popc(K);
         // output: bits of positions p0 + 32*lane + b
-        if (K && P.bits) {
+        if (K && seg.bits) {
           const uint64_t gpos = p0 + 32ull * lane;
           const uint32_t sh = (uint32_t)(gpos & 31u);
           const uint64_t gword = gpos >> 5;
           if (sh == 0) {
-            atomicOr(&P.bits[gword], K);
+            atomicOr(&seg.bits[gword], K);
           } else {
             const uint32_t a = K << sh, b = K >> (32u - sh);
-            if (a) atomicOr(&P.bits[gword], a);
-            if (b) atomicOr(&P.bits[gword + 1], b);
+            if (a) atomicOr(&seg.bits[gword], a);
+            if (b) atomicOr(&seg.bits[gword + 1], b);
           }
         }
       }

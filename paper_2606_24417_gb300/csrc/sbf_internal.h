@@ -23,6 +23,10 @@ struct sbf_filter {
   uint32_t* host_dev_bits[2] = {nullptr, nullptr};
   uint32_t* host_dev_hits[2] = {nullptr, nullptr};
   uint64_t host_cap_seq = 0, host_cap_reads = 0;
+  // pinned landing slots for each chunk's first answer word (a pageable
+  // destination would make the copy synchronous and stall the pipeline)
+  uint32_t* host_first = nullptr;
+  uint64_t host_first_cap = 0;
 };
 
 namespace sbf {

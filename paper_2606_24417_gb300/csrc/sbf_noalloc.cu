@@ -118,8 +118,11 @@ extern "C" int sbf_batch_query_noalloc(sbf_filter* const* filters, int n_filters
       Segment sg{};
       sg.words = filters[fi]->geom.words;
       sg.n_shards = filters[fi]->geom.n_shards;
+      sg.seq = d_seq;
+      sg.seq_len = seq_len;
       sg.off = d_off + g0;
       sg.n_reads = g1 - g0;
+      sg.bits = d_kmer_bits;
       sg.hits = d_read_hits ? d_read_hits + g0 : nullptr;
       sg.iter_begin = iters;
       if (g1 > g0) {
@@ -144,9 +147,6 @@ extern "C" int sbf_batch_query_noalloc(sbf_filter* const* filters, int n_filters
     return cuda_fail(e, "memset");
   Params P{};
   P.g = f0->geom;
-  P.seq = d_seq;
-  P.seq_len = seq_len;
-  P.bits = d_kmer_bits;
   P.stats = nullptr;
   P.segs = d_table;
   P.n_segs = (uint32_t)n_filters;

@@ -83,7 +83,6 @@ struct Request {
   uint32_t* h_bits = nullptr;
   uint64_t seq_at = 0, seq_bytes = 0;    // placement in the read arena
   uint64_t meta_at = 0, meta_bytes = 0;  // offsets + hits in the meta arena
-  std::vector<uint64_t> off_abs;         // offsets rebased to the arena
   uint64_t kmers = 0;
   Clock::time_point t_submit, t_done;
   int state = 0;                         // 0 queued, 1 in flight, 2 done, < 0 error code
@@ -146,17 +145,20 @@ int start_launch(sbf_server* s, Launch& L) {
     uint64_t* d_off = reinterpret_cast<uint64_t*>(s->d_meta + r->meta_at);
     uint32_t* d_hits = reinterpret_cast<uint32_t*>(d_off + r->n_reads + 1);
     if ((e = cudaMemcpyAsync(s->d_seq + r->seq_at, r->h_seq, r->seq_len, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(d_off, r->off_abs.data(), (r->n_reads + 1) * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_off, r->h_off, (r->n_reads + 1) * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(d_hits, 0, r->n_reads * 4, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(s->d_bits + r->seq_at / 32, 0, r->seq_bytes / 8, st)) != cudaSuccess)
       return cuda_fail(e, "server staging");
     Segment sg{};
     sg.words = g.words;
     sg.n_shards = g.n_shards;
+    sg.seq = s->d_seq + r->seq_at;   // the request's own bytes, offsets as submitted
+    sg.seq_len = r->seq_len;
     sg.off = d_off;
     sg.n_reads = r->n_reads;
+    sg.bits = s->d_bits + r->seq_at / 32;
     sg.hits = d_hits;
-    sg.p_begin = r->seq_at;
+    sg.p_begin = 0;
     sg.iter_begin = iters;
     sg.iters = (r->seq_len + adv - 1) / adv;
     iters += sg.iters;
@@ -167,9 +169,6 @@ int start_launch(sbf_server* s, Launch& L) {
     return cuda_fail(e, "server table upload");
   Params P{};
   P.g = g;
-  P.seq = s->d_seq;
-  P.seq_len = s->seq_arena->size();
-  P.bits = s->d_bits;
   P.stats = nullptr;
   P.segs = s->d_tables[slot];
   P.n_segs = (uint32_t)L.reqs.size();
@@ -245,8 +244,6 @@ void worker_loop(sbf_server* s) {
         }
         r->seq_at = sa;
         r->meta_at = ma;
-        r->off_abs.resize(r->n_reads + 1);
-        for (uint64_t i = 0; i <= r->n_reads; ++i) r->off_abs[i] = sa + r->h_off[i];
         r->state = 1;
         s->queue.pop_front();
         L.reqs.push_back(r);
