@@ -161,9 +161,9 @@ def kernel_source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
+def profiled_counter(kernel: str, key: str):
+    """A per-launch ncu counter from the committed summary, if it was taken on
+    the current kernel sources; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -172,7 +172,38 @@ def profiled_traffic(kernel: str):
     e = d.get(kernel)
     if not e or e.get("source_digest") != kernel_source_digest():
         return None
-    return e.get("dram_bytes_per_launch")
+    return e.get(key)
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)."""
+    return profiled_counter(kernel, "dram_bytes_per_launch")
+
+
+def sector_bandwidth(dev, stream, buf_bytes: int, sector_bytes: int, rmw: bool, n: int,
+                     reps: int = 5):
+    """Median GB/s of the random-sector probe (n sectors per launch) over a
+    buffer of buf_bytes: loaded bytes for a gather, read + written bytes for a
+    read-modify-write."""
+    import torch
+
+    from paper_2606_24417_gb300.sbf import probe_sectors
+
+    buf = torch.zeros(buf_bytes, dtype=torch.uint8, device=dev)
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    for r in range(2):
+        probe_sectors(buf, sector_bytes, n, seed=r, rmw=rmw, sink=sink, stream=stream)
+    ms = []
+    for r in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        probe_sectors(buf, sector_bytes, n, seed=100 + r, rmw=rmw, sink=sink, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    del buf
+    moved = n * sector_bytes * (2 if rmw else 1)
+    return moved / (statistics.median(ms) / 1e3) / 1e9
 
 
 # ---------------------------------------------------------------------------
@@ -382,6 +413,52 @@ def run_ours(args, rank, world, local_rank):
                 "frac": achieved / peak, "traffic": profiled_traffic(dominant),
                 "kernel": dominant, "peak_kind": f"{peak_kind} (copy bandwidth)",
                 "algorithmic_bytes_per_launch": d_bytes, "launch_ms": d_ms}
+    # ---- shard part against the random-sector probe; issue-slot bound -----
+    sector_b = SHARD_BITS // 8
+    big = 1 << 30  # 1 GiB >= 4x L2: every probe access goes to DRAM
+    filt = FILTER_BITS // 8
+    bw = {"gather_dram": sector_bandwidth(dev, stream, big, sector_b, False, 1 << 27),
+          "gather_filter_size": sector_bandwidth(dev, stream, filt, sector_b, False, 1 << 27),
+          "rmw_dram": sector_bandwidth(dev, stream, big, sector_b, True, 1 << 25),
+          "rmw_filter_size": sector_bandwidth(dev, stream, filt, sector_b, True, 1 << 25)}
+    q_stream = q_bytes - runs_q * sector_b
+    i_stream = genome.nbytes
+
+    def bound(kmers, stream_bytes, shard_bytes, shard_gbs):
+        t = stream_bytes / (peak * 1e9) + shard_bytes / (shard_gbs * 1e9)
+        return kmers / t
+
+    q_rate, i_rate = q_kmers / (q_ms / 1e3), ins_kmers / (ins_ms / 1e3)
+    sector_roofline = {
+        "unit": "k-mers/s",
+        "probe_gbs": bw,
+        "sector_bytes": sector_b,
+        "query": {"bound_dram": bound(q_kmers, q_stream, runs_q * sector_b, bw["gather_dram"]),
+                  "bound_filter_size": bound(q_kmers, q_stream, runs_q * sector_b,
+                                             bw["gather_filter_size"]),
+                  "achieved": q_rate},
+        "insert": {"bound_dram": bound(ins_kmers, i_stream, runs_i * 2 * sector_b, bw["rmw_dram"]),
+                   "bound_filter_size": bound(ins_kmers, i_stream, runs_i * 2 * sector_b,
+                                              bw["rmw_filter_size"]),
+                   "achieved": i_rate},
+        "note": "streamed bytes at the copy peak plus shard bytes at the probe's random-sector "
+                "bandwidth; 'dram' probes a 1 GiB buffer, 'filter_size' a buffer the size of "
+                "the filter (part of it stays in L2)",
+    }
+    for part in ("query", "insert"):
+        e = sector_roofline[part]
+        e["frac_dram"] = e["achieved"] / e["bound_dram"]
+        e["frac_filter_size"] = e["achieved"] / e["bound_filter_size"]
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    issue_peak = n_sm * 4 * sm_mhz * 1e6  # 4 schedulers per SM, one warp instruction per cycle
+    inst = profiled_counter(dominant, "warp_inst_per_launch")
+    alu = {"bound": "alu", "unit": "warp instructions/s", "kernel": dominant,
+           "peak": issue_peak, "peak_kind": f"{n_sm} SMs x 4 schedulers x 1 instr/cycle x "
+                                            f"{sm_mhz:.0f} MHz (median SM clock sampled)",
+           "warp_inst_per_launch": inst,
+           "achieved": inst / (d_ms / 1e3) if inst else None,
+           "frac": inst / (d_ms / 1e3) / issue_peak if inst else None}
     cpu = cpu_baseline(genome, reads, roff) if world == 1 else None
     line = {
         "metric": METRIC, "value": value, "unit": "k-mers/s", "n_gpus": world,
@@ -398,6 +475,8 @@ def run_ours(args, rank, world, local_rank):
         "insert_ms": ins_ms, "query_ms": q_ms,
         "runs_per_kmer": {"query": runs_q / max(valid_q, 1), "insert": runs_i / max(valid_i, 1)},
         "roofline": roofline,
+        "sector_roofline": sector_roofline,
+        "alu": alu,
         "e2e": {"value": e2e_value, "unit": "k-mers/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "answers_match_device": same},
         "gpu_launches": 2 * args.steps,

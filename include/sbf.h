@@ -256,6 +256,28 @@ int sbf_server_reset_stats(sbf_server* s);
  * offset table (valid or not). */
 int sbf_num_kmers(const uint64_t* h_off, uint64_t n_reads, int k, uint64_t* out);
 
+/* ---------------------------------------------------------------------------
+ * Random-sector bandwidth probe.  Measurement only; not a step of the method.
+ *
+ * Inserts and queries touch one shard of shard_bits/8 bytes per super-k-mer
+ * run at a hashed position (Alg. 1 flush, Alg. 2 shard load), so their shard
+ * traffic is bounded by the bandwidth of random sector-sized accesses, not by
+ * a streaming copy.  This call measures that ceiling on the caller's buffer:
+ *  rmw = 0: n loads of one whole random sector each (sector_bytes / 16 lanes
+ *           of 16 bytes, sector-aligned);
+ *  rmw = 1: n read-modify-writes, one 64-bit atomicOr of a nonzero mask into
+ *           every word of a random sector (the buffer's bits change).
+ * Sector i of the sequence is floor(mix64(seed + i) * (buf_bytes /
+ * sector_bytes) / 2^64) with mix64 the SplitMix64 finaliser, so a run with the
+ * same arguments touches the same sectors.  d_buf: device, 64-byte aligned,
+ * buf_bytes >= sector_bytes; sector_bytes: 32 or 64; d_sink: one device
+ * uint64 the gather may add to (keeps its loads live; contents meaningless).
+ * Asynchronous on `stream`; time it with events.  Algorithmic bytes: n *
+ * sector_bytes (gather), 2 * n * sector_bytes (read-modify-write).
+ * ------------------------------------------------------------------------- */
+int sbf_probe_sectors(void* d_buf, uint64_t buf_bytes, int sector_bytes, uint64_t n,
+                      uint64_t seed, int rmw, uint64_t* d_sink, sbf_stream_t stream);
+
 /* Human-readable reason of the calling thread's last failure ("" if none). */
 const char* sbf_last_error(void);
 

@@ -82,6 +82,7 @@ def load_library() -> ctypes.CDLL:
                                            ctypes.POINTER(ctypes.c_uint32)]),
             "sbf_batch_tune": (I, [P, I, P, U64, P, P, U64, P, U32P, U32P, P,
                                    ctypes.POINTER(ctypes.c_float)]),
+            "sbf_probe_sectors": (I, [P, U64, I, U64, U64, I, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -426,6 +427,20 @@ def batch_query_noalloc(filters, seq, off, off_host, group, bits, hits, stream=N
                                        _dev_ptr(off, 8), _host_ptr(oh), oh.size - 1, _host_ptr(gr),
                                        _dev_ptr(bits, 4), _dev_ptr(hits, 4), _stream_handle(stream)))
     return bits, hits
+
+
+def probe_sectors(buf, sector_bytes: int, n: int, seed: int = 0, rmw: bool = False, sink=None,
+                  stream=None) -> None:
+    """Random-sector bandwidth probe over the device tensor `buf` (measurement
+    only): n random sector loads, or n atomicOr read-modify-writes of a whole
+    sector when `rmw`.  Asynchronous; time it with CUDA events."""
+    import torch
+
+    lib = load_library()
+    if sink is None:
+        sink = torch.zeros(1, dtype=torch.int64, device=buf.device)
+    _check(lib.sbf_probe_sectors(_dev_ptr(buf), buf.numel() * buf.element_size(), sector_bytes, n,
+                                 seed, 1 if rmw else 0, _dev_ptr(sink, 8), _stream_handle(stream)))
 
 
 def num_kmers(off: np.ndarray, k: int) -> int:

@@ -69,3 +69,13 @@ def test_num_kmers_host(lib):
 
 def test_destroy_null_is_noop(lib):
     lib.sbf_destroy(None)
+
+
+def test_probe_argument_checks_without_gpu(lib):
+    buf = ctypes.create_string_buffer(256)
+    sink = ctypes.c_uint64(0)
+    # unsupported sector size and NULL pointers are refused before any CUDA call
+    assert lib.sbf_probe_sectors(ctypes.addressof(buf), 256, 48, 1, 0, 0,
+                                 ctypes.addressof(sink), None) == -1
+    assert lib.sbf_probe_sectors(None, 256, 64, 1, 0, 0, ctypes.addressof(sink), None) == -1
+    assert lib.sbf_probe_sectors(ctypes.addressof(buf), 256, 64, 1, 0, 0, None, None) == -1
