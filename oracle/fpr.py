@@ -28,12 +28,15 @@ def findere_fpr(eps: float, k: int, s: int) -> float:
     return eps ** (k - s + 1)
 
 
-def sector_layout(H: int, shard_bits: int):
-    """(S sectors, sector_bits, c_j counts) of the sectorised shard."""
+def sector_layout(H: int, shard_bits: int, layout: int = 0):
+    """(S sectors, sector_bits, c_j counts) of the sectorised shard.  Layout 1
+    (the paper's, Sec. IV-B) makes every 64-bit word a sector, used or not."""
     W = shard_bits // 64
     S = 1
     while 2 * S <= min(H, W):   # largest power of two not above min(H, W)
         S *= 2
+    if layout == 1:
+        S = W
     sector_bits = shard_bits // S
     c = np.array([sum(1 for i in range(H) if i % S == j) for j in range(S)], dtype=np.int64)
     return S, sector_bits, c
@@ -45,32 +48,34 @@ def _popcount_u64(a: np.ndarray) -> np.ndarray:
     return np.unpackbits(b, axis=-1).sum(axis=-1).astype(np.int64)
 
 
-def sector_fill(words: np.ndarray, H: int, shard_bits: int) -> np.ndarray:
+def sector_fill(words: np.ndarray, H: int, shard_bits: int, layout: int = 0) -> np.ndarray:
     """f[x, j]: fraction of set bits in sector j of shard x."""
-    S, sector_bits, _ = sector_layout(H, shard_bits)
+    S, sector_bits, _ = sector_layout(H, shard_bits, layout)
     W = shard_bits // 64
     pc = _popcount_u64(np.asarray(words, dtype=np.uint64)).reshape(-1, W)
     per_sector = pc.reshape(pc.shape[0], S, W // S).sum(axis=2)
     return per_sector / float(sector_bits)
 
 
-def conditional_fpr(words: np.ndarray, k: int, s: int, H: int, shard_bits: int) -> float:
+def conditional_fpr(words: np.ndarray, k: int, s: int, H: int, shard_bits: int,
+                    layout: int = 0) -> float:
     """Expected false-positive rate of a random alien k-mer on this filter."""
-    _, _, c = sector_layout(H, shard_bits)
-    f = sector_fill(words, H, shard_bits)
+    _, _, c = sector_layout(H, shard_bits, layout)
+    f = sector_fill(words, H, shard_bits, layout)
     expo = (k - s + 1) * c
+    used = expo > 0  # sectors no hash addresses (layout 1, H < 4) do not count
     with np.errstate(divide="ignore"):
-        logp = (np.log(f) * expo[None, :]).sum(axis=1)
+        logp = (np.log(f[:, used]) * expo[None, used]).sum(axis=1)
     return float(np.exp(logp).mean())
 
 
-def blocked_bloom_fpr(n: int, n_shards: int, H: int, shard_bits: int) -> float:
+def blocked_bloom_fpr(n: int, n_shards: int, H: int, shard_bits: int, layout: int = 0) -> float:
     """A-priori FPR of the s = k reduction: n distinct items in n_shards blocks.
 
     The load of a block is Poisson(n / n_shards); an item puts c_j bits into
     sector j, so a sector with load L is filled to 1 - (1 - 1/sector_bits)^(L c_j).
     """
-    S, sector_bits, c = sector_layout(H, shard_bits)
+    S, sector_bits, c = sector_layout(H, shard_bits, layout)
     lam = n / n_shards
     total = 0.0
     L = 0

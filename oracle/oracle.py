@@ -48,6 +48,8 @@ def _load():
         I = ctypes.c_int
         lib.oracle_create.restype = P
         lib.oracle_create.argtypes = [I, I, I, I, I, I, U64]
+        lib.oracle_create_layout.restype = P
+        lib.oracle_create_layout.argtypes = [I, I, I, I, I, I, U64, I]
         lib.oracle_destroy.argtypes = [P]
         lib.oracle_destroy.restype = None
         lib.oracle_num_shards.argtypes = [P]
@@ -92,17 +94,18 @@ class OracleSBF:
     """Plain CPU Super Bloom filter with the library's parameter domain."""
 
     def __init__(self, k: int, m: int, s: int, H: int, bits: int, shard_bits: int = 512,
-                 canonical: bool = True):
+                 canonical: bool = True, layout: int = 0):
         lib = _load()
-        h = lib.oracle_create(k, m, s, H, shard_bits, 1 if canonical else 0, bits)
+        h = lib.oracle_create_layout(k, m, s, H, shard_bits, 1 if canonical else 0, bits, layout)
         if not h:
             raise ValueError(f"invalid oracle parameters k={k} m={m} s={s} H={H} "
-                             f"shard_bits={shard_bits} bits={bits}")
+                             f"shard_bits={shard_bits} bits={bits} layout={layout}")
         self._h = ctypes.c_void_p(h)
         self._lib = lib
         self.k, self.m, self.s, self.H = k, m, s, H
         self.shard_bits = shard_bits
         self.canonical = bool(canonical)
+        self.layout = layout
         self.n_shards = int(lib.oracle_num_shards(self._h))
         self.n_words = int(lib.oracle_num_words(self._h))
 

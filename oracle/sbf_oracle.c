@@ -25,6 +25,11 @@
  *              m-mer domain, so two different m-mers never tie.
  *   mix64:     the SplitMix64 finaliser (Steele, Lea, Flood 2014).
  *   shard:     x = floor(mix64(mu ^ 0x14057B7EF767814F) * N / 2^64).
+ *   paper layout (layout = 1, Sec. IV-B and Alg. 1/2 taken literally):
+ *              256-bit shards, N rounded up to a power of two, shard =
+ *              order key of mu AND (N - 1), and every 64-bit word is its
+ *              own sector (hash i in word i mod 4, b = 6), so for H < 4 some
+ *              words of each shard stay unused.
  *   s-mer:     h = mix64(v ^ 0x5851F42D4C957F2D) (the stronger mix, Sec. IV-G).
  *   layout:    shard x owns bits [x*B, (x+1)*B) of a little-endian array of
  *              64-bit words.  W = B/64 words, S = the largest power of two
@@ -53,7 +58,7 @@
 #define ORACLE_SHARD_KEY 0x14057B7EF767814FULL
 
 struct oracle_sbf {
-  int k, m, s, H, B, canonical;
+  int k, m, s, H, B, canonical, layout;
   uint64_t N;      /* shards */
   uint64_t words;  /* 64-bit words = N * B / 64 */
   uint64_t* bits;
@@ -114,7 +119,10 @@ static uint64_t mix64(uint64_t x) {
   return x;
 }
 
+static uint64_t order_key(uint64_t v, int m);
+
 static uint64_t shard_of(const oracle_sbf* f, uint64_t mu) {
+  if (f->layout == 1) return order_key(mu, f->m) & (f->N - 1);  /* minHash & (NumShards - 1) */
   unsigned __int128 prod = (unsigned __int128)mix64(mu ^ ORACLE_SHARD_KEY) * f->N;
   return (uint64_t)(prod >> 64);
 }
@@ -126,7 +134,8 @@ static int log2_exact(int v) {
 }
 
 /* Bit index inside the shard for hash function i of s-mer hash h. */
-static int sector_count(int H, int W) {
+static int sector_count(const oracle_sbf* f, int H, int W) {
+  if (f->layout == 1) return W;  /* one 64-bit word per sector */
   int lim = H < W ? H : W;
   int S = 1;
   while (2 * S <= lim) S *= 2;
@@ -135,7 +144,7 @@ static int sector_count(int H, int W) {
 
 static uint64_t bit_in_shard(const oracle_sbf* f, uint64_t h, int i) {
   int W = f->B / 64;
-  int S = sector_count(f->H, W);
+  int S = sector_count(f, f->H, W);
   int sector_bits = f->B / S;
   int b = log2_exact(sector_bits);
   int q = 64 / f->H;
@@ -205,13 +214,26 @@ static int kmer_valid(const oracle_sbf* f, const uint8_t* seq, uint64_t p, uint6
 
 oracle_sbf* oracle_create(int k, int m, int s, int H, int shard_bits, int canonical,
                           uint64_t bits) {
+  return oracle_create_layout(k, m, s, H, shard_bits, canonical, bits, 0);
+}
+
+oracle_sbf* oracle_create_layout(int k, int m, int s, int H, int shard_bits, int canonical,
+                                 uint64_t bits, int layout) {
+  if (layout != 0 && layout != 1) return NULL;
+  if (layout == 1 && shard_bits != 256) return NULL;
   if (k < 1 || k > 32 || m < 1 || m > k || s < 1 || s > k || H < 1 || H > 16) return NULL;
   if (shard_bits != 256 && shard_bits != 512) return NULL;
   if (bits < (uint64_t)shard_bits) return NULL;
   oracle_sbf* f = (oracle_sbf*)calloc(1, sizeof(oracle_sbf));
   if (!f) return NULL;
   f->k = k; f->m = m; f->s = s; f->H = H; f->B = shard_bits; f->canonical = canonical ? 1 : 0;
+  f->layout = layout;
   f->N = (bits + (uint64_t)shard_bits - 1) / (uint64_t)shard_bits;
+  if (layout == 1) { /* round the shard count up to a power of two */
+    uint64_t n = 1;
+    while (n < f->N) n <<= 1;
+    f->N = n;
+  }
   f->words = f->N * (uint64_t)(shard_bits / 64);
   f->bits = (uint64_t*)calloc(f->words, sizeof(uint64_t));
   if (!f->bits) {

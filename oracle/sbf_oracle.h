@@ -31,6 +31,11 @@ typedef struct oracle_sbf oracle_sbf;
 /* Returns NULL on invalid parameters (same domain as the library). */
 oracle_sbf* oracle_create(int k, int m, int s, int H, int shard_bits, int canonical,
                           uint64_t bits);
+/* layout 0: this library's layout (the default); layout 1: the paper's
+ * literal layout (256-bit shards only; N rounded up to a power of two, shard
+ * = minimizer order key & (N - 1), hash i in 64-bit word i mod 4). */
+oracle_sbf* oracle_create_layout(int k, int m, int s, int H, int shard_bits, int canonical,
+                                 uint64_t bits, int layout);
 void oracle_destroy(oracle_sbf* f);
 
 uint64_t oracle_num_shards(const oracle_sbf* f);

@@ -32,10 +32,14 @@ def mix64(x: int) -> int:
 
 
 class BruteSBF:
-    def __init__(self, k, m, s, H, bits, shard_bits=512, canonical=True):
+    def __init__(self, k, m, s, H, bits, shard_bits=512, canonical=True, layout=0):
         self.k, self.m, self.s, self.H, self.B = k, m, s, H, shard_bits
         self.canonical = canonical
+        self.layout = layout
         self.N = -(-bits // shard_bits)
+        if layout == 1:  # the paper's literal layout: 2^P shards of 256 bits
+            assert shard_bits == 256
+            self.N = 1 << (self.N - 1).bit_length()
         self.pairs = set()
 
     def canon(self, x: str) -> int:
@@ -52,6 +56,8 @@ class BruteSBF:
         return min(mmers, key=self.key)
 
     def shard(self, kmer: str) -> int:
+        if self.layout == 1:  # shardIdx = minHash & (NumShards - 1), Alg. 1
+            return self.key(self.minimizer(kmer)) & (self.N - 1)
         return (mix64(self.minimizer(kmer) ^ 0x14057B7EF767814F) * self.N) >> 64
 
     def smers(self, kmer: str):
@@ -61,7 +67,7 @@ class BruteSBF:
         """Absolute bit indices of canonical s-mer v in shard x."""
         h = mix64(v ^ 0x5851F42D4C957F2D)
         W = self.B // 64
-        S = 1 << (min(self.H, W).bit_length() - 1)
+        S = W if self.layout == 1 else 1 << (min(self.H, W).bit_length() - 1)
         sector_bits = self.B // S
         b = sector_bits.bit_length() - 1
         q = 64 // self.H

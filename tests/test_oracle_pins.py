@@ -16,7 +16,7 @@ import pytest
 from bruteforce import BruteSBF, revcomp
 from oracle import OracleSBF
 from oracle.fpr import (binomial_two_sided_p, blocked_bloom_fpr, bloom_fpr,
-                        conditional_fpr)
+                        conditional_fpr, sector_fill, sector_layout)
 from oracle.oracle import runs_of_keys
 from paper_2606_24417_gb300 import synth
 
@@ -85,6 +85,13 @@ CONFIGS = [
     (32, 16, 30, 4, 1 << 15, 512, True),   # k = 32
     (31, 16, 28, 3, 1 << 15, 512, True),   # H = 3: two sectors
     (31, 16, 28, 6, 1 << 15, 256, True),   # H = 6: four sectors, two slices share one
+    # the paper's literal layout (layout 1): 2^P shards, key & (N - 1), word sectors
+    (31, 16, 28, 4, 1 << 15, 256, False, 1),  # the paper's operating point, forward only
+    (31, 16, 28, 2, 3000 * 256, 256, False, 1),  # N rounded up; words 2, 3 unused
+    (31, 16, 28, 12, 1 << 15, 256, True, 1),  # q = 5 < 6: salted multiply
+    (31, 16, 28, 16, 1 << 15, 256, False, 1),  # q = 4
+    (31, 20, 31, 8, 1 << 14, 256, True, 1),   # 64-bit order key
+    (9, 5, 6, 2, 4096, 256, False, 1),        # Fig. 2 parameters
 ]
 
 
@@ -100,13 +107,14 @@ def _tiny_reads(rng, k):
 
 @pytest.mark.parametrize("cfg", CONFIGS)
 def test_bruteforce_filter_and_answers(cfg):
-    k, m, s, H, bits, B, canon = cfg
+    k, m, s, H, bits, B, canon, *rest = cfg
+    layout = rest[0] if rest else 0
     rng = random.Random(hash(cfg) & 0xFFFF)
     reads = _tiny_reads(rng, k)
     seq, off = _reads_to_arrays(reads)
-    f = OracleSBF(k, m, s, H, bits, shard_bits=B, canonical=canon)
+    f = OracleSBF(k, m, s, H, bits, shard_bits=B, canonical=canon, layout=layout)
     f.insert(seq, off)
-    b = BruteSBF(k, m, s, H, bits, shard_bits=B, canonical=canon)
+    b = BruteSBF(k, m, s, H, bits, shard_bits=B, canonical=canon, layout=layout)
     for r in reads:
         b.insert_read(r)
     assert np.array_equal(f.words(), b.words())
@@ -270,6 +278,94 @@ def test_fpr_matches_conditional_closed_form(bits, H, B, s):
     X = int(hits.sum())
     assert p_hat > 1e-4
     assert binomial_two_sided_p(X, Q, p_hat) > 1e-4, (X, Q * p_hat)
+
+
+def _paper_shards_numpy(qseq, Q, k, m, n_shards, canonical):
+    """Shards of Q length-k reads under layout 1, vectorised in numpy from the
+    definition (a third implementation, sharing nothing with the C oracle):
+    minimizer = m-mer of least key (v * 0x9E3779B9) mod 2^32, shard = key & (N - 1)."""
+    code = np.full(256, 0, dtype=np.uint64)
+    for ch, c in zip(b"ACGTacgt", (0, 1, 2, 3, 0, 1, 2, 3)):
+        code[ch] = c
+    x = code[np.asarray(qseq, dtype=np.uint8).reshape(Q, k)]
+    best_key = None
+    for i in range(k - m + 1):
+        fwd = np.zeros(Q, dtype=np.uint64)
+        rc = np.zeros(Q, dtype=np.uint64)
+        for j in range(m):
+            fwd = (fwd << np.uint64(2)) | x[:, i + j]
+            rc = rc | ((np.uint64(3) - x[:, i + j]) << np.uint64(2 * j))
+        v = np.minimum(fwd, rc) if canonical else fwd
+        key = (v * np.uint64(0x9E3779B9)) & np.uint64(0xFFFFFFFF)
+        best_key = key if best_key is None else np.minimum(best_key, key)
+    return (best_key & np.uint64(n_shards - 1)).astype(np.int64)
+
+
+@pytest.mark.parametrize("bits,H,s,canonical", [
+    (1 << 22, 4, 28, False),
+    (1 << 22, 2, 28, True),
+    (3 << 20, 8, 26, False),   # 12,288 shards rounded up to 16,384
+])
+def test_paper_layout_fpr_matches_conditional_closed_form(bits, H, s, canonical):
+    """Layout 1 under the shard-aware form of Eq. 2, conditioned on each
+    alien's shard: with shardIdx = minHash & (N - 1) an alien's shard is not
+    uniform (minimizer suffixes are biased and the same bias loads those
+    shards more), so the uniform-shard average understates the rate by a few
+    percent.  Given the shards, the alien's s-mers are independent of the
+    filter and X has mean sum_q g(x_q) and variance sum_q g(1 - g), with
+    g(x) = prod_j f[x, j]^((k-s+1) c_j)."""
+    g = _genome(1_000_000, 0)
+    f = OracleSBF(31, 16, s, H, bits, shard_bits=256, canonical=canonical, layout=1)
+    f.insert(g, np.array([0, g.size], dtype=np.uint64))
+    Q = 1_000_000
+    qseq, qoff = _alien_kmers(Q, seed=78)
+    _, hits = f.query(qseq, qoff)
+    X = int(hits.sum())
+    _, _, c = sector_layout(H, 256, layout=1)
+    fill = sector_fill(f.words(), H, 256, layout=1)
+    used = c > 0
+    gx = np.prod(fill[:, used] ** ((31 - s + 1) * c[None, used]), axis=1)
+    shards = _paper_shards_numpy(qseq, Q, 31, 16, f.n_shards, canonical)
+    mean = float(gx[shards].sum())
+    sd = float((gx[shards] * (1 - gx[shards])).sum()) ** 0.5
+    assert mean > 100
+    assert abs(X - mean) <= 4.5 * sd + 3, (X, mean, sd)
+    # the uniform-shard form is the same quantity averaged over all shards
+    p_uniform = conditional_fpr(f.words(), 31, s, H, 256, layout=1)
+    assert abs(p_uniform - float(gx.mean())) <= 1e-12 + 1e-9 * p_uniform
+
+
+def test_paper_layout_shard_count_and_unused_words():
+    """Sec. IV-B: 2^P shards (count rounded up), hash i in 64-bit word i mod 4,
+    so with H < 4 words H..3 of every shard are never set."""
+    g = _genome(100_000, 9)
+    off = np.array([0, g.size], dtype=np.uint64)
+    for H in (1, 2, 3, 4):
+        f = OracleSBF(31, 16, 28, H, 5000 * 256, shard_bits=256, layout=1)
+        assert f.n_shards == 8192
+        f.insert(g, off)
+        w = f.words().reshape(-1, 4)
+        for j in range(4):
+            assert (np.count_nonzero(w[:, j]) > 0) == (j < H), (H, j)
+
+
+def test_paper_layout_shard_depends_on_minimizer_suffix():
+    """shardIdx = minHash & (N - 1) with a multiplicative minHash (Alg. 1): the
+    low P bits of v * C (C odd) depend only on the low P bits of v, so k-mers
+    whose minimizers end in the same P/2 bases share a shard, and distinct
+    minimizer suffixes map to distinct shards (C odd is invertible mod 2^P)."""
+    rng = random.Random(11)
+    f = OracleSBF(31, 16, 28, 4, 1 << 20, shard_bits=256, canonical=False, layout=1)
+    P = f.n_shards.bit_length() - 1
+    assert f.n_shards == 1 << P
+    by_suffix = {}
+    for _ in range(3000):
+        km = _random_dna(rng, 31)
+        mu, x = f.kmer_info(np.frombuffer(km.encode(), dtype=np.uint8))
+        by_suffix.setdefault(mu & ((1 << P) - 1), set()).add(x)
+    assert all(len(v) == 1 for v in by_suffix.values())
+    shards = [next(iter(v)) for v in by_suffix.values()]
+    assert len(set(shards)) == len(shards)
 
 
 def test_blocked_bloom_reduction_s_equals_k():
