@@ -707,6 +707,126 @@ def run_sweep(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# the paper's parameter sweep (Sec. V-B, Fig. 5) on its literal layout
+# ---------------------------------------------------------------------------
+PAPER_SWEEP_CLAIMS = {
+    # (numerator point, denominator point): ratios the paper quotes (Sec. V-B)
+    "H8_vs_H4": ((28, 16, 8), (28, 16, 4), {"fpr": 2.0, "total_time": 1.076}),
+    "H16_vs_H4": ((28, 16, 16), (28, 16, 4), {"fpr": 5.2, "total_time": 1.659}),
+    "s28_vs_s16": ((28, 16, 4), (16, 16, 4), {"fpr": 1 - 0.374, "total_time": 1 - 0.291}),
+    "s30_vs_s28": ((30, 16, 4), (28, 16, 4), {"fpr": 1.256}),
+    "s31_vs_s28": ((31, 16, 4), (28, 16, 4), {"fpr": 2.29}),
+    "m12_vs_m8": ((28, 12, 4), (28, 8, 4), {"fpr": 1 - 0.917}),
+    "m16_vs_m12": ((28, 16, 4), (28, 12, 4), {"fpr": 1 - 0.908}),
+    "m18_vs_m16": ((28, 18, 4), (28, 16, 4), {"fpr": 1.035, "total_time": 1.085}),
+    "m31_vs_m16": ((28, 31, 4), (28, 16, 4), {"fpr": 4.8, "insert_time": 7.7}),
+}
+
+
+def paper_sweep_points():
+    pts = [(28, 16, h) for h in (4, 8, 12, 16)]
+    pts += [(s, 16, 4) for s in (16, 20, 24, 26, 27, 28, 29, 30, 31)]
+    pts += [(28, m, 4) for m in (8, 10, 12, 14, 16, 18, 20, 24, 31)]
+    pts += [(s, m, h) for s in (24, 26, 28, 30, 31) for m in (12, 14, 16, 20)
+            for h in (4, 8, 12, 16)]
+    seen, out = set(), []
+    for p in pts:
+        if p not in seen:
+            seen.add(p)
+            out.append(p)
+    return out
+
+
+def run_paper_sweep(args):
+    """(s, m, H) at k = 31 on the paper's layout (256-bit shards, 2^P of them,
+    shard = minimizer key & (2^P - 1), forward strand only) with its 256 MiB
+    budget, on the 100 Mbp bacterial-shaped genome standing in for C. elegans.
+    Every point is timed on the generic one-k-mer-per-thread kernels (the
+    paper's thread mapping) and, where one exists, on the fused kernel."""
+    import torch
+
+    from paper_2606_24417_gb300 import build_lib, synth
+    from paper_2606_24417_gb300.sbf import LAYOUT_PAPER, SuperBloomFilter
+    from paper_2606_24417_gb300.stats import expected_fpr
+
+    build_lib.build()
+    torch.cuda.set_device(0)
+    genome = synth.bacterial_genome(GENOME_BP, seed=2)
+    n_s = n_r = 1_000_000
+    reads, roff = synth.mixed_query_reads(genome, n_s, n_r, READ_LEN, 0.01, seed=3)
+    dg = torch.from_numpy(genome).cuda()
+    dgo = torch.from_numpy(np.array([0, genome.size], dtype=np.int64)).cuda()
+    dq = torch.from_numpy(reads).cuda()
+    dqo = torch.from_numpy(roff.astype(np.int64)).cuda()
+    bits_out = torch.empty((reads.size + 31) // 32, dtype=torch.int32, device="cuda")
+    hits = torch.empty(n_s + n_r, dtype=torch.int32, device="cuda")
+    rand_kmers = n_r * (READ_LEN - K + 1)
+    budget_bits = 256 * 8 * (1 << 20)  # 256 MiB
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def timed(f):
+        f.clear()
+        f.insert(dg, dgo)
+        f.query(dq, dqo, bits=bits_out, hits=hits)   # warm
+        f.clear()
+        e[0].record()
+        f.insert(dg, dgo)
+        e[1].record()
+        f.query(dq, dqo, bits=bits_out, hits=hits)
+        e[2].record()
+        torch.cuda.synchronize()
+        return e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+
+    points = {}
+    for (s, m, h) in paper_sweep_points():
+        rec = {"s": s, "m": m, "H": h}
+        for variant in ("generic", "fused"):
+            if variant == "generic":
+                os.environ["SBF_FORCE_GENERIC"] = "1"
+            else:
+                os.environ.pop("SBF_FORCE_GENERIC", None)
+            f = SuperBloomFilter(K, m, s, h, budget_bits, shard_bits=256, canonical=False,
+                                 layout=LAYOUT_PAPER)
+            if variant == "fused" and not f.fused:
+                f.close()
+                continue
+            ins_ms, q_ms = timed(f)
+            rec[variant] = {"insert_ms": ins_ms, "query_ms": q_ms, "total_ms": ins_ms + q_ms}
+            if variant == "generic":
+                fp = int(hits[n_s:].sum().item())
+                words = f.words()
+                rec["fpr_measured"] = fp / rand_kmers
+                rec["false_positives"] = fp
+                rec["fpr_expected_uniform_shard"] = expected_fpr(words, K, s, h, 256, layout=1)
+            else:   # both kernels give the same answers
+                assert int(hits[n_s:].sum().item()) == rec["false_positives"]
+            f.close()
+        points[(s, m, h)] = rec
+    os.environ.pop("SBF_FORCE_GENERIC", None)
+
+    claims = {}
+    for name, (num, den, paper) in PAPER_SWEEP_CLAIMS.items():
+        a, b = points[num], points[den]
+        got = {"fpr": a["fpr_measured"] / b["fpr_measured"] if b["fpr_measured"] else None}
+        for kern in ("generic", "fused"):
+            if kern in a and kern in b:
+                got[f"total_time_{kern}"] = a[kern]["total_ms"] / b[kern]["total_ms"]
+                got[f"insert_time_{kern}"] = a[kern]["insert_ms"] / b[kern]["insert_ms"]
+        claims[name] = {"ours": got, "paper": paper}
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    with open(os.path.join(ROOT, "gpurun_out", "paper_sweep.json"), "w") as fh:
+        json.dump({"points": list(points.values()), "claims": claims}, fh)
+    print(json.dumps({"workload": "paper sweep: k=31, (s, m, H) axes through (28, 16, 4) and the "
+                      "s x m x H grid with H in {4,8,12,16}; paper layout (256-bit shards, "
+                      "key & (2^P - 1), forward strand), 256 MiB filter; 100 Mbp "
+                      "bacterial-shaped genome; 1M sampled + 1M random 150 bp query reads "
+                      "(FPR from the random half)",
+                      "points": len(points), "claims": claims,
+                      "written": "gpurun_out/paper_sweep.json"}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -715,7 +835,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: 2M query reads (300 MB, still larger than L2) for profiling")
-    ap.add_argument("--workload", default="bacterial", choices=["bacterial", "batched", "served", "sweep"],
+    ap.add_argument("--workload", default="bacterial",
+                    choices=["bacterial", "batched", "served", "sweep", "paper_sweep"],
                     help="batched: the many-filter workload (its own JSON line)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="device-timed steps only (no e2e, no CPU baseline): profiling runs")
@@ -734,6 +855,8 @@ def main():
         return run_served(args) if rank == 0 else 0
     if args.workload == "sweep":
         return run_sweep(args) if rank == 0 else 0
+    if args.workload == "paper_sweep":
+        return run_paper_sweep(args) if rank == 0 else 0
     if world > 1:
         import torch
         import torch.distributed as dist

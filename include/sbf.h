@@ -83,6 +83,22 @@ enum {
 int sbf_create(int k, int m, int s, int H, uint64_t bits, sbf_filter** out);
 int sbf_create_ex(int k, int m, int s, int H, uint64_t bits, int shard_bits, int canonical,
                   sbf_filter** out);
+
+/* Shard layouts.  SBF_LAYOUT_DEFAULT is the layout described above (any N,
+ * shard = multiply-high of a mixed minimizer, min(H, W) sectors rounded down
+ * to a power of two).  SBF_LAYOUT_PAPER is Sec. IV-B with Alg. 1/2 taken
+ * literally: shard_bits must be 256, N is rounded UP to a power of two,
+ * the shard is the minimizer's order key & (N - 1) (so it depends only on
+ * the minimizer's last log2(N)/2 bases), and hash i sets a bit of 64-bit word
+ * i mod 4 (b = 6; for H < 4 words H..3 stay zero; bit-slicing while
+ * floor(64/H) >= 6, the salted multiply beyond, Sec. IV-G).  sbf_create_ex is
+ * sbf_create_layout with SBF_LAYOUT_DEFAULT.  The fused kernels serve the
+ * paper layout for H in {4, 8}; other H use the generic kernels. */
+enum { SBF_LAYOUT_DEFAULT = 0, SBF_LAYOUT_PAPER = 1 };
+int sbf_create_layout(int k, int m, int s, int H, uint64_t bits, int shard_bits, int canonical,
+                      int layout, sbf_filter** out);
+/* The filter's layout (SBF_LAYOUT_*), or SBF_EINVAL for NULL. */
+int sbf_layout(const sbf_filter* f);
 /* Frees the device memory.  NULL is a no-op.  Must not be called while work
  * on the filter is in flight. */
 void sbf_destroy(sbf_filter* f);
@@ -255,6 +271,39 @@ int sbf_server_reset_stats(sbf_server* s);
 /* Number of k-mer start positions sum_r max(0, len_r - k + 1) of a host
  * offset table (valid or not). */
 int sbf_num_kmers(const uint64_t* h_off, uint64_t n_reads, int k, uint64_t* out);
+
+/* ---------------------------------------------------------------------------
+ * FASTA / FASTQ input (host side; Sec. IV-A streamed FASTX input, Sec. IV-F
+ * sequence-native records).
+ *
+ * An incremental parser that turns FASTX text, fed in chunks of any size,
+ * into read batches for sbf_*_seqs_host: sequence bytes of one or more
+ * records back to back, `n_pieces + 1` offsets, and for each piece the index
+ * of its record (0, 1, ... in file order; FASTA '>' and FASTQ '@' records may
+ * be mixed).  Header lines, FASTQ '+' lines and qualities are skipped; line
+ * breaks, CR, spaces and tabs inside sequence lines are dropped; every other
+ * byte is copied (non-ACGT bytes such as N are invalid and break k-mers,
+ * Sec. IV-F).  A record that does not fit the output buffer is split: its
+ * next piece (in the next call) starts with the record's last k-1 bases, so
+ * each k-mer of a record lies in exactly one piece.  Summing the per-read
+ * hits of sbf_query_seqs_host over a record's pieces gives the record's hits.
+ *
+ * sbf_fastx_create: k sets the k-1 bases carried into a split record's next
+ *   piece.  The parser owns no caller memory.
+ * sbf_fastx_parse: parses text[0, *consumed) into seq (capacity seq_cap
+ *   bytes, at least 2(k-1) + 64), off (pieces_cap + 1 entries) and rec
+ *   (pieces_cap entries).  It stops early when either output is full; the
+ *   caller feeds text[*consumed, text_len) again (with the next chunk
+ *   appended if it likes).  final = 1 marks text_len as the end of the input
+ *   (the open record ends).  A record may yield zero-length pieces.
+ * ------------------------------------------------------------------------- */
+typedef struct sbf_fastx sbf_fastx;
+int sbf_fastx_create(int k, sbf_fastx** out);
+void sbf_fastx_destroy(sbf_fastx* p);
+int sbf_fastx_parse(sbf_fastx* p, const uint8_t* text, uint64_t text_len, int final,
+                    uint8_t* seq, uint64_t seq_cap, uint64_t* off, uint64_t* rec,
+                    uint64_t pieces_cap, uint64_t* n_pieces, uint64_t* seq_len,
+                    uint64_t* consumed);
 
 /* ---------------------------------------------------------------------------
  * Random-sector bandwidth probe.  Measurement only; not a step of the method.

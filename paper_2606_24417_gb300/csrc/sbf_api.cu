@@ -106,14 +106,24 @@ extern "C" {
 
 const char* sbf_last_error(void) { return g_err; }
 
-int sbf_create_ex(int k, int m, int s, int H, uint64_t bits, int shard_bits, int canonical,
-                  sbf_filter** out) {
+int sbf_create_layout(int k, int m, int s, int H, uint64_t bits, int shard_bits, int canonical,
+                      int layout, sbf_filter** out) {
   clear_error();
   if (!out) return fail(SBF_EINVAL, "out is NULL");
   *out = nullptr;
   int rc = check_params(k, m, s, H, bits, shard_bits);
   if (rc != SBF_OK) return rc;
+  if (layout != SBF_LAYOUT_DEFAULT && layout != SBF_LAYOUT_PAPER)
+    return fail(SBF_EINVAL, "layout must be 0 or 1 (got %d)", layout);
+  if (layout == SBF_LAYOUT_PAPER && shard_bits != 256)
+    return fail(SBF_EINVAL, "the paper's layout has 256-bit shards (got %d)", shard_bits);
   uint64_t n_shards = (bits + (uint64_t)shard_bits - 1) / (uint64_t)shard_bits;
+  if (layout == SBF_LAYOUT_PAPER) {  // 2^P shards
+    if (n_shards > (1ull << 56)) return fail(SBF_EINVAL, "filter too large");
+    uint64_t p2 = 1;
+    while (p2 < n_shards) p2 <<= 1;
+    n_shards = p2;
+  }
   uint64_t n_words = n_shards * (uint64_t)(shard_bits / 64);
   sbf_filter* f = new (std::nothrow) sbf_filter();
   if (!f) return fail(SBF_ENOMEM, "host allocation failed");
@@ -136,16 +146,23 @@ int sbf_create_ex(int k, int m, int s, int H, uint64_t bits, int shard_bits, int
     delete f;
     return cuda_fail(e, "cudaMemset");
   }
-  f->geom = make_geom(words, n_shards, k, m, s, H, shard_bits, canonical ? 1 : 0);
+  f->geom = make_geom(words, n_shards, k, m, s, H, shard_bits, canonical ? 1 : 0, layout);
   f->n_words = n_words;
   f->fused = fused_supported(f->geom);
   *out = f;
   return SBF_OK;
 }
 
-int sbf_create(int k, int m, int s, int H, uint64_t bits, sbf_filter** out) {
-  return sbf_create_ex(k, m, s, H, bits, 512, 1, out);
+int sbf_create_ex(int k, int m, int s, int H, uint64_t bits, int shard_bits, int canonical,
+                  sbf_filter** out) {
+  return sbf_create_layout(k, m, s, H, bits, shard_bits, canonical, SBF_LAYOUT_DEFAULT, out);
 }
+
+int sbf_create(int k, int m, int s, int H, uint64_t bits, sbf_filter** out) {
+  return sbf_create_layout(k, m, s, H, bits, 512, 1, SBF_LAYOUT_DEFAULT, out);
+}
+
+int sbf_layout(const sbf_filter* f) { return f ? f->geom.layout : SBF_EINVAL; }
 
 void sbf_destroy(sbf_filter* f) {
   if (!f) return;

@@ -284,7 +284,7 @@ int sbf_batch_create(sbf_filter* const* filters, int n_filters, sbf_batch** out)
     if (!filters[i]) return fail(SBF_EINVAL, "filter %d is NULL", i);
     const sbf::Geom& g = filters[i]->geom;
     if (g.k != g0.k || g.m != g0.m || g.s != g0.s || g.H != g0.H || g.shard_bits != g0.shard_bits ||
-        g.canonical != g0.canonical)
+        g.canonical != g0.canonical || g.layout != g0.layout)
       return fail(SBF_EINVAL, "filter %d has different parameters", i);
     if (!filters[i]->fused)
       return fail(SBF_EUNSUPPORTED, "filter %d has no fused kernel (batching needs one)", i);

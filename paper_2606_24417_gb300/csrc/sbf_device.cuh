@@ -32,24 +32,30 @@ struct Geom {
   int k, m, s, H;
   int shard_bits;      // B
   int canonical;
-  int sectors;         // S = largest power of two <= min(H, B/64)
+  int layout;          // 0: this library's layout; 1: the paper's literal one
+  int sectors;         // S = largest power of two <= min(H, B/64); B/64 for layout 1
   int sector_bits;     // B / S
   int sector_log2;     // b = log2(B / S)
   int slice;           // q = floor(64 / H)
 };
 
+// Layout 1 is Sec. IV-B and Alg. 1/2 taken literally: 2^P shards (the caller
+// rounds N up), shard = minimizer order key & (N - 1), and every 64-bit word
+// is a sector (hash i in word i mod W; with H < W some words stay unused).
 __host__ __device__ inline Geom make_geom(uint64_t* words, uint64_t n_shards, int k, int m, int s,
-                                          int H, int shard_bits, int canonical) {
+                                          int H, int shard_bits, int canonical, int layout = 0) {
   Geom g;
   g.words = words;
   g.n_shards = n_shards;
   g.k = k; g.m = m; g.s = s; g.H = H;
   g.shard_bits = shard_bits;
   g.canonical = canonical;
+  g.layout = layout;
   int W = shard_bits / 64;
   int lim = H < W ? H : W;  // sectors: the largest power of two not above min(H, W)
   g.sectors = 1;
   while (2 * g.sectors <= lim) g.sectors *= 2;
+  if (layout == 1) g.sectors = W;
   g.sector_bits = shard_bits / g.sectors;
   int b = 0;
   while ((1 << b) < g.sector_bits) ++b;
@@ -85,6 +91,12 @@ __device__ __forceinline__ uint64_t order_key(uint64_t v, int m) {
 
 __device__ __forceinline__ uint64_t shard_of(uint64_t mu, uint64_t n_shards) {
   return __umul64hi(mix64(mu ^ kShardKey), n_shards);
+}
+
+// Shard of minimizer mu under either layout (layout 1: n_shards is 2^P).
+__device__ __forceinline__ uint64_t shard_of(const Geom& g, uint64_t mu) {
+  if (g.layout == 1) return order_key(mu, g.m) & (g.n_shards - 1);
+  return shard_of(mu, g.n_shards);
 }
 
 __device__ __forceinline__ uint64_t smer_hash(uint64_t v) { return mix64(v ^ kSmerKey); }

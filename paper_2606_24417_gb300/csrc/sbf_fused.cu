@@ -60,6 +60,8 @@ bool fused_supported(const Geom& g) {
   if (w != 12 && w != 16 && w != 18 && w != 20) return false;
   if ((2 * g.m > 32) != fused::key64_for(w)) return false;
   if (g.H != 1 && g.H != 2 && g.H != 4 && g.H != 8) return false;
+  // the fused address packs use min(H, W) sectors; layout 1 always has W
+  if (g.layout == 1 && g.H < g.shard_bits / 64) return false;
   // 32-bit slot entries hold the shard index unless the order key is 64-bit
   if (!fused::key64_for(w) && g.n_shards > (1ull << 32)) return false;
 #ifdef SBF_MINIMAL_GRID

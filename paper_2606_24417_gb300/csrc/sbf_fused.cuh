@@ -190,7 +190,7 @@ struct Segment {
 };
 
 struct Params {
-  Geom g;                 // shared k, m, s, H, shard bits, canonical
+  Geom g;                 // shared k, m, s, H, shard bits, canonical, layout
   uint64_t* stats;        // query: valid k-mers, runs, positives, or NULL
   const Segment* segs;    // NULL: the launch is the single segment seg0
   uint32_t n_segs;
@@ -637,14 +637,20 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
 
     // ---------------- shards of the runs: index, then async copy ----------
     const uint64_t n_shards = g.n_shards;
+    const bool masked = g.layout == 1;  // the paper's shard rule: key & (2^P - 1)
     for (uint32_t si = lane; si < total_slots; si += 32) {
-      uint64_t mu;
-      if constexpr (KEY64) {
-        mu = S.slot_x[si] * inv64(kGolden64);
+      uint64_t x;
+      if (masked) {
+        x = (uint64_t)S.slot_x[si] & (n_shards - 1);
       } else {
-        mu = (uint32_t)S.slot_x[si] * inv32(kGolden32);
+        uint64_t mu;
+        if constexpr (KEY64) {
+          mu = S.slot_x[si] * inv64(kGolden64);
+        } else {
+          mu = (uint32_t)S.slot_x[si] * inv32(kGolden32);
+        }
+        x = __umul64hi(mix64(mu ^ kShardKey), n_shards);
       }
-      uint64_t x = __umul64hi(mix64(mu ^ kShardKey), n_shards);
       S.slot_x[si] = (typename Sm::SlotT)x;
       if (si < (uint32_t)kSlotCap) {
         if constexpr (INSERT) {

@@ -73,7 +73,7 @@ __global__ void generic_insert_kernel(Geom g, const uint8_t* __restrict__ seq, u
   for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < seq_len; p += stride) {
     KmerView v = load_kmer(g, seq, seq_len, off, n_reads, p);
     if (!v.valid) continue;
-    uint64_t x = shard_of(minimizer(g, v.fwd, v.rc), g.n_shards);
+    uint64_t x = shard_of(g, minimizer(g, v.fwd, v.rc));
     uint64_t base = x * (uint64_t)g.shard_bits;
     for (int t = 0; t <= g.k - g.s; ++t) {
       uint64_t h = smer_hash(canon(g, v.fwd, v.rc, t, g.s));
@@ -95,7 +95,7 @@ __global__ void generic_query_kernel(Geom g, const uint8_t* __restrict__ seq, ui
     KmerView v = load_kmer(g, seq, seq_len, off, n_reads, p);
     if (!v.valid) continue;
     uint64_t mu = minimizer(g, v.fwd, v.rc);
-    uint64_t x = shard_of(mu, g.n_shards);
+    uint64_t x = shard_of(g, mu);
     uint64_t base = x * (uint64_t)g.shard_bits;
     bool present = true;
     for (int t = 0; t <= g.k - g.s && present; ++t) {

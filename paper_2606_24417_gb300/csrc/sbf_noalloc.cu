@@ -84,7 +84,8 @@ extern "C" int sbf_batch_query_noalloc(sbf_filter* const* filters, int n_filters
     if (!f) return fail(SBF_EINVAL, "filter %d is NULL", i);
     if (f->geom.k != f0->geom.k || f->geom.m != f0->geom.m || f->geom.s != f0->geom.s ||
         f->geom.H != f0->geom.H || f->geom.shard_bits != f0->geom.shard_bits ||
-        f->geom.canonical != f0->geom.canonical || f->device != f0->device)
+        f->geom.canonical != f0->geom.canonical ||
+        f->geom.layout != f0->geom.layout || f->device != f0->device)
       return fail(SBF_EINVAL, "filter %d differs in parameters or device", i);
     if (!f->fused) return fail(SBF_EUNSUPPORTED, "filter %d has no fused kernel", i);
   }

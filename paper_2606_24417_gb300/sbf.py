@@ -48,6 +48,8 @@ def load_library() -> ctypes.CDLL:
         sig = {
             "sbf_create": (I, [I, I, I, I, U64, ctypes.POINTER(P)]),
             "sbf_create_ex": (I, [I, I, I, I, U64, I, I, ctypes.POINTER(P)]),
+            "sbf_create_layout": (I, [I, I, I, I, U64, I, I, I, ctypes.POINTER(P)]),
+            "sbf_layout": (I, [P]),
             "sbf_destroy": (None, [P]),
             "sbf_info": (I, [P] + [ctypes.POINTER(I)] * 6 + [ctypes.POINTER(U64)]),
             "sbf_num_words": (U64, [P]),
@@ -83,6 +85,10 @@ def load_library() -> ctypes.CDLL:
             "sbf_batch_tune": (I, [P, I, P, U64, P, P, U64, P, U32P, U32P, P,
                                    ctypes.POINTER(ctypes.c_float)]),
             "sbf_probe_sectors": (I, [P, U64, I, U64, U64, I, P, P]),
+            "sbf_fastx_create": (I, [I, ctypes.POINTER(P)]),
+            "sbf_fastx_destroy": (None, [P]),
+            "sbf_fastx_parse": (I, [P, P, U64, I, P, U64, P, P, U64, ctypes.POINTER(U64),
+                                    ctypes.POINTER(U64), ctypes.POINTER(U64)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -127,15 +133,18 @@ class SuperBloomFilter:
 
     k, m, s, H: k-mer, minimizer and Findere s-mer lengths and hash count;
     bits: filter size (rounded up to whole shards); shard_bits: 256 or 512;
-    canonical: treat a k-mer and its reverse complement as one key.
+    canonical: treat a k-mer and its reverse complement as one key;
+    layout: LAYOUT_DEFAULT, or LAYOUT_PAPER for the paper's literal layout
+    (256-bit shards, 2^P of them, shard = minimizer key & (2^P - 1), hash i
+    in 64-bit word i mod 4).
     """
 
     def __init__(self, k: int = 31, m: int = 16, s: int = 28, H: int = 4, bits: int = 1 << 30,
-                 shard_bits: int = 512, canonical: bool = True):
+                 shard_bits: int = 512, canonical: bool = True, layout: int = 0):
         lib = load_library()
         h = ctypes.c_void_p()
-        _check(lib.sbf_create_ex(k, m, s, H, bits, shard_bits, 1 if canonical else 0,
-                                 ctypes.byref(h)))
+        _check(lib.sbf_create_layout(k, m, s, H, bits, shard_bits, 1 if canonical else 0, layout,
+                                     ctypes.byref(h)))
         self._h = h
         self._lib = lib
         ki, mi, si, Hi, Bi, ci = (ctypes.c_int() for _ in range(6))
@@ -146,6 +155,7 @@ class SuperBloomFilter:
         self.shard_bits, self.canonical = Bi.value, bool(ci.value)
         self.n_shards = int(n.value)
         self.n_words = int(lib.sbf_num_words(h))
+        self.layout = int(lib.sbf_layout(h))
 
     def close(self) -> None:
         h = getattr(self, "_h", None)
@@ -210,10 +220,10 @@ class SuperBloomFilter:
                                               off.size - 1))
 
     def query_host(self, seq: np.ndarray, off: np.ndarray, bits: np.ndarray | None = None,
-                   hits: np.ndarray | None = None):
+                   hits: np.ndarray | None = None, want_bits: bool = True):
         seq = np.ascontiguousarray(seq, dtype=np.uint8)
         off = np.ascontiguousarray(off, dtype=np.uint64)
-        if bits is None:
+        if bits is None and want_bits:
             bits = np.empty((seq.size + 31) // 32, dtype=np.uint32)
         if hits is None:
             hits = np.empty(off.size - 1, dtype=np.uint32)
@@ -234,32 +244,34 @@ class SuperBloomFilter:
         _check(self._lib.sbf_set_bits(self._h, _host_ptr(w)))
 
     _MAGIC = b"SBFGB300"
-    _VERSION = 1
+    _VERSION = 2  # version 1 had no layout field (layout 0)
 
     def save(self, path: str) -> None:
         """Checkpoint: header (magic, version, k, m, s, H, shard_bits,
-        canonical, n_shards) followed by the raw little-endian words."""
-        hdr = struct.pack("<8sIiiiiiiQ", self._MAGIC, self._VERSION, self.k, self.m, self.s,
-                          self.H, self.shard_bits, int(self.canonical), self.n_shards)
+        canonical, n_shards, layout) followed by the raw little-endian words."""
+        hdr = struct.pack("<8sIiiiiiiQi", self._MAGIC, self._VERSION, self.k, self.m, self.s,
+                          self.H, self.shard_bits, int(self.canonical), self.n_shards, self.layout)
         with open(path, "wb") as fh:
             fh.write(hdr)
             fh.write(self.words().astype("<u8").tobytes())
 
     @classmethod
     def load(cls, path: str) -> "SuperBloomFilter":
-        size = struct.calcsize("<8sIiiiiiiQ")
+        size1 = struct.calcsize("<8sIiiiiiiQ")
         with open(path, "rb") as fh:
-            hdr = fh.read(size)
+            hdr = fh.read(size1)
             magic, ver, k, m, s, H, B, canon, n = struct.unpack("<8sIiiiiiiQ", hdr)
-            if magic != cls._MAGIC or ver != cls._VERSION:
+            if magic != cls._MAGIC or ver not in (1, 2):
                 raise SbfError(-1, f"{path}: not a filter checkpoint")
-            f = cls(k, m, s, H, n * B, shard_bits=B, canonical=bool(canon))
+            layout = struct.unpack("<i", fh.read(4))[0] if ver == 2 else 0
+            f = cls(k, m, s, H, n * B, shard_bits=B, canonical=bool(canon), layout=layout)
             w = np.frombuffer(fh.read(), dtype="<u8")
             f.set_words(w)
         return f
 
 
 BATCH_PER_FILTER, BATCH_FUSED, BATCH_GRAPH = 0, 1, 2
+LAYOUT_DEFAULT, LAYOUT_PAPER = 0, 1
 
 
 class FilterBatch:

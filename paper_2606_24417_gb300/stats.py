@@ -19,14 +19,22 @@ def _popcount64(a: np.ndarray) -> np.ndarray:
     return np.unpackbits(b, axis=-1).sum(axis=-1).astype(np.int64)
 
 
-def expected_fpr(words: np.ndarray, k: int, s: int, H: int, shard_bits: int) -> float:
+def expected_fpr(words: np.ndarray, k: int, s: int, H: int, shard_bits: int,
+                 layout: int = 0) -> float:
+    """Layout 1 (the paper's) has one sector per 64-bit word; sectors no hash
+    uses (H < 4) do not enter the product.  Under layout 1 an alien's shard is
+    only close to uniform (it is the low bits of its minimizer key), so this
+    is the uniform-shard approximation there."""
     w64 = shard_bits // 64
     sectors = min(H, w64)
     while sectors & (sectors - 1):   # largest power of two not above min(H, W)
         sectors &= sectors - 1
+    if layout == 1:
+        sectors = w64
     per_sector = _popcount64(np.asarray(words, dtype=np.uint64)).reshape(-1, sectors, w64 // sectors).sum(axis=2)
     fill = per_sector / float(shard_bits // sectors)
     uses = np.array([sum(1 for i in range(H) if i % sectors == j) for j in range(sectors)])
+    used = uses > 0
     with np.errstate(divide="ignore"):
-        logp = (np.log(fill) * ((k - s + 1) * uses)[None, :]).sum(axis=1)
+        logp = (np.log(fill[:, used]) * ((k - s + 1) * uses[used])[None, :]).sum(axis=1)
     return float(np.exp(logp).mean())

@@ -79,3 +79,14 @@ def test_probe_argument_checks_without_gpu(lib):
                                  ctypes.addressof(sink), None) == -1
     assert lib.sbf_probe_sectors(None, 256, 64, 1, 0, 0, ctypes.addressof(sink), None) == -1
     assert lib.sbf_probe_sectors(ctypes.addressof(buf), 256, 64, 1, 0, 0, None, None) == -1
+
+
+def test_layout_argument_checks_without_gpu(lib):
+    import ctypes as C
+
+    h = C.c_void_p()
+    # the paper layout has 256-bit shards; unknown layouts are refused
+    assert lib.sbf_create_layout(31, 16, 28, 4, 1 << 20, 512, 0, 1, C.byref(h)) == -1
+    assert lib.sbf_create_layout(31, 16, 28, 4, 1 << 20, 256, 0, 2, C.byref(h)) == -1
+    assert not h.value
+    assert lib.sbf_layout(None) == -1

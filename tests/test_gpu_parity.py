@@ -43,16 +43,18 @@ def u32(t):
     return t.cpu().numpy().view(np.uint32)
 
 
-def make_filter(k, m, s, H, bits, B=512, canonical=True):
+def make_filter(k, m, s, H, bits, B=512, canonical=True, layout=0):
     from paper_2606_24417_gb300.sbf import SuperBloomFilter
 
-    return SuperBloomFilter(k, m, s, H, bits, shard_bits=B, canonical=canonical)
+    return SuperBloomFilter(k, m, s, H, bits, shard_bits=B, canonical=canonical, layout=layout)
 
 
 def check_insert_query(params, ins_seq, ins_off, q_seq, q_off, check_stats=True):
-    k, m, s, H, bits, B, canon = params
-    f = make_filter(k, m, s, H, bits, B, canon)
-    o = OracleSBF(k, m, s, H, bits, shard_bits=B, canonical=canon)
+    k, m, s, H, bits, B, canon, *rest = params
+    layout = rest[0] if rest else 0
+    f = make_filter(k, m, s, H, bits, B, canon, layout)
+    o = OracleSBF(k, m, s, H, bits, shard_bits=B, canonical=canon, layout=layout)
+    assert f.n_shards == o.n_shards
     f.insert(dev(ins_seq), dev_off(ins_off))
     o.insert(ins_seq, ins_off)
     assert np.array_equal(f.words(), o.words()), f"words differ for {params}"
@@ -122,6 +124,14 @@ PARAMS = [
     (9, 5, 6, 2, 1 << 16, 256, True),       # Fig. 2 parameters
     (32, 16, 30, 4, 1 << 22, 512, True),
     (21, 11, 17, 12, 5000 * 512, 512, True),
+    # the paper's literal layout (Sec. IV-B, Alg. 1/2): k, m, s, H, bits, B, canonical, layout
+    (31, 16, 28, 4, 1 << 21, 256, False, 1),     # fused
+    (31, 16, 28, 8, 3_000_000, 256, True, 1),    # fused; 11,719 shards rounded up to 16,384
+    (31, 20, 24, 4, 1 << 22, 256, True, 1),      # fused, 64-bit order keys
+    (31, 12, 24, 8, 1 << 22, 256, False, 1),     # fused, w = 20
+    (31, 16, 28, 2, 1 << 21, 256, False, 1),     # generic: words 2, 3 unused
+    (31, 16, 28, 12, 1 << 21, 256, False, 1),    # generic: salted multiply (Fig. 5 H = 12)
+    (31, 16, 28, 16, 1 << 21, 256, True, 1),     # generic: H = 16
 ]
 
 
@@ -211,19 +221,29 @@ def test_host_path_matches_device(monkeypatch, params):
     assert np.array_equal(hb2, ob) and np.array_equal(hh2, oh)
 
 
-def test_checkpoint_roundtrip(tmp_path):
-    params = (31, 16, 28, 4, 1 << 20, 256, False)
+@pytest.mark.parametrize("layout", [0, 1])
+def test_checkpoint_roundtrip(tmp_path, layout):
+    params = (31, 16, 28, 4, 1000 * 256, 256, False)
     seq, off = ragged_reads(500, 41)
-    f = make_filter(*params[:5], params[5], params[6])
+    f = make_filter(*params[:5], params[5], params[6], layout)
     f.insert(dev(seq), dev_off(off))
     p = tmp_path / "f.sbf"
     f.save(str(p))
     g = type(f).load(str(p))
-    assert (g.k, g.m, g.s, g.H, g.shard_bits, g.canonical) == (31, 16, 28, 4, 256, False)
+    assert (g.k, g.m, g.s, g.H, g.shard_bits, g.canonical, g.layout, g.n_shards) == \
+        (31, 16, 28, 4, 256, False, layout, f.n_shards)
     assert np.array_equal(f.words(), g.words())
     qb1, qh1 = f.query(dev(seq), dev_off(off))
     qb2, qh2 = g.query(dev(seq), dev_off(off))
     assert torch.equal(qb1, qb2) and torch.equal(qh1, qh2)
+
+
+def test_paper_layout_kernel_choice():
+    assert make_filter(31, 16, 28, 4, 1 << 20, 256, False, 1).fused
+    assert make_filter(31, 16, 28, 8, 1 << 20, 256, False, 1).fused
+    assert not make_filter(31, 16, 28, 2, 1 << 20, 256, False, 1).fused
+    f = make_filter(31, 16, 28, 4, 3 * 256 * 1000, 256, False, 1)
+    assert f.n_shards == 4096 and f.layout == 1
 
 
 def test_fused_grid_is_used():
