@@ -805,6 +805,19 @@ def run_paper_sweep(args):
         points[(s, m, h)] = rec
     os.environ.pop("SBF_FORCE_GENERIC", None)
 
+    # the same budget and points on this library's default layout (mixed
+    # minimizer -> any shard), to show what the mask rule costs
+    default_layout = {}
+    for (s, m, h) in ((28, 16, 4), (28, 16, 8), (28, 12, 4), (31, 16, 4)):
+        f = SuperBloomFilter(K, m, s, h, budget_bits, shard_bits=256, canonical=False)
+        ins_ms, q_ms = timed(f)
+        fp = int(hits[n_s:].sum().item())
+        default_layout[f"{s},{m},{h}"] = {
+            "fpr_measured": fp / rand_kmers, "false_positives": fp,
+            "fpr_paper_layout": points[(s, m, h)]["fpr_measured"],
+            "insert_ms": ins_ms, "query_ms": q_ms, "fused": f.fused}
+        f.close()
+
     claims = {}
     for name, (num, den, paper) in PAPER_SWEEP_CLAIMS.items():
         a, b = points[num], points[den]
@@ -816,14 +829,125 @@ def run_paper_sweep(args):
         claims[name] = {"ours": got, "paper": paper}
     os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
     with open(os.path.join(ROOT, "gpurun_out", "paper_sweep.json"), "w") as fh:
-        json.dump({"points": list(points.values()), "claims": claims}, fh)
+        json.dump({"points": list(points.values()), "claims": claims,
+                   "default_layout": default_layout}, fh)
     print(json.dumps({"workload": "paper sweep: k=31, (s, m, H) axes through (28, 16, 4) and the "
                       "s x m x H grid with H in {4,8,12,16}; paper layout (256-bit shards, "
                       "key & (2^P - 1), forward strand), 256 MiB filter; 100 Mbp "
                       "bacterial-shaped genome; 1M sampled + 1M random 150 bp query reads "
                       "(FPR from the random half)",
                       "points": len(points), "claims": claims,
+                      "default_layout_same_budget": default_layout,
                       "written": "gpurun_out/paper_sweep.json"}), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# host-resident FASTA / FASTQ input (Sec. IV-A streamed FASTX, Sec. V-F)
+# ---------------------------------------------------------------------------
+def run_fastx(args):
+    """Insert the bacterial genome from a FASTA file and query 2M reads from a
+    FASTQ file (plain and gzip) through the streaming reader; beside them the
+    same work from host arrays and from device-resident inputs."""
+    import gzip
+    import shutil
+    import tempfile
+
+    import torch
+
+    from paper_2606_24417_gb300 import build_lib, synth
+    from paper_2606_24417_gb300.fastx import insert_fastx, query_fastx
+    from paper_2606_24417_gb300.sbf import SuperBloomFilter
+
+    build_lib.build()
+    torch.cuda.set_device(0)
+    genome = synth.bacterial_genome(GENOME_BP, seed=2)
+    n_s = n_r = 1_000_000
+    reads, roff = synth.mixed_query_reads(genome, n_s, n_r, READ_LEN, 0.01, seed=3)
+    tmp = tempfile.mkdtemp(prefix="sbf_fastx_")
+    try:
+        t = time.perf_counter()
+        fa = os.path.join(tmp, "genome.fa")
+        with open(fa, "wb") as fh:
+            fh.write(b">genome synthetic 100 Mbp\n")
+            lines = np.full((genome.size + 59) // 60 * 61, ord("\n"), dtype=np.uint8)
+            full = genome.size // 60
+            lines[:full * 61].reshape(full, 61)[:, :60] = genome[:full * 60].reshape(full, 60)
+            rest = genome.size - full * 60
+            if rest:
+                lines[full * 61:full * 61 + rest] = genome[full * 60:]
+                lines = lines[:full * 61 + rest + 1]
+            fh.write(lines.tobytes())
+        fq = os.path.join(tmp, "reads.fq")
+        n = roff.size - 1
+        rec = np.empty((n, 3 + READ_LEN + 3 + READ_LEN + 1), dtype=np.uint8)
+        rec[:, 0] = ord("@")
+        rec[:, 1] = ord("r")
+        rec[:, 2] = ord("\n")
+        rec[:, 3:3 + READ_LEN] = reads.reshape(n, READ_LEN)
+        rec[:, 3 + READ_LEN:6 + READ_LEN] = np.frombuffer(b"\n+\n", dtype=np.uint8)
+        rec[:, 6 + READ_LEN:6 + 2 * READ_LEN] = ord("I")
+        rec[:, -1] = ord("\n")
+        with open(fq, "wb") as fh:
+            fh.write(rec.tobytes())
+        fqz = fq + ".gz"
+        with open(fq, "rb") as src, gzip.open(fqz, "wb", compresslevel=1) as dst:
+            shutil.copyfileobj(src, dst, 16 << 20)
+        log(f"[bench] FASTX files written in {time.perf_counter() - t:.1f}s")
+        ins_kmers = genome.size - K + 1
+        q_kmers = n * (READ_LEN - K + 1)
+        f = SuperBloomFilter(K, M, S, H, FILTER_BITS, shard_bits=SHARD_BITS)
+
+        def best(fn, reps=3):
+            ts = []
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                out = fn()
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            return min(ts), out
+
+        res = {}
+        t_ins, info = best(lambda: (f.clear(), insert_fastx(f, fa))[1])
+        res["fasta_insert"] = {"kmers_per_s": ins_kmers / t_ins, "seconds": t_ins,
+                               "text_bytes": info["text_bytes"],
+                               "parse_seconds": info["parse_seconds"], "batches": info["batches"]}
+        want = f.words()
+        for name, path in (("fastq_query", fq), ("fastq_gz_query", fqz)):
+            t_q, (hits, kmers, qi) = best(lambda: query_fastx(f, path))
+            res[name] = {"kmers_per_s": q_kmers / t_q, "seconds": t_q,
+                         "text_bytes": qi["text_bytes"], "parse_seconds": qi["parse_seconds"],
+                         "batches": qi["batches"], "positives": int(hits.sum())}
+        # the same work from host arrays and from device-resident inputs
+        h_genome = torch.from_numpy(genome).pin_memory().numpy()
+        h_goff = np.array([0, genome.size], dtype=np.uint64)
+        h_reads = torch.from_numpy(reads).pin_memory().numpy()
+        h_roff = torch.from_numpy(roff.view(np.int64)).pin_memory().numpy().view(np.uint64)
+        t_hi, _ = best(lambda: (f.clear(), f.insert_host(h_genome, h_goff)))
+        same = bool(np.array_equal(f.words(), want))
+        t_hq, (_, hh) = best(lambda: f.query_host(h_reads, h_roff, want_bits=False))
+        dg = torch.from_numpy(genome).cuda()
+        dgo = torch.from_numpy(h_goff.astype(np.int64)).cuda()
+        dq = torch.from_numpy(reads).cuda()
+        dqo = torch.from_numpy(roff.astype(np.int64)).cuda()
+        hits_d = torch.empty(n, dtype=torch.int32, device="cuda")
+        t_di, _ = best(lambda: (f.clear(), f.insert(dg, dgo)))
+        t_dq, _ = best(lambda: f.query(dq, dqo, hits=hits_d, want_bits=False))
+        agree = int(hh.astype(np.int64).sum()) == res["fastq_query"]["positives"] == \
+            res["fastq_gz_query"]["positives"] == int(hits_d.sum().item())
+        res["host_arrays"] = {"insert_kmers_per_s": ins_kmers / t_hi,
+                              "query_kmers_per_s": q_kmers / t_hq}
+        res["device_resident"] = {"insert_kmers_per_s": ins_kmers / t_di,
+                                  "query_kmers_per_s": q_kmers / t_dq,
+                                  "note": "wall clock around one launch (host timer)"}
+        print(json.dumps({"workload": "fastx: 100 Mbp bacterial-shaped genome as FASTA (60-column "
+                          "lines) inserted; 1M sampled + 1M random 150 bp reads as FASTQ (plain "
+                          "and gzip level 1) queried; per-record hits",
+                          "results": res, "filters_identical": same, "answers_agree": agree,
+                          "host_cores": os.cpu_count()}), flush=True)
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
     return 0
 
 
@@ -836,7 +960,7 @@ def main():
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: 2M query reads (300 MB, still larger than L2) for profiling")
     ap.add_argument("--workload", default="bacterial",
-                    choices=["bacterial", "batched", "served", "sweep", "paper_sweep"],
+                    choices=["bacterial", "batched", "served", "sweep", "paper_sweep", "fastx"],
                     help="batched: the many-filter workload (its own JSON line)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="device-timed steps only (no e2e, no CPU baseline): profiling runs")
@@ -857,6 +981,8 @@ def main():
         return run_sweep(args) if rank == 0 else 0
     if args.workload == "paper_sweep":
         return run_paper_sweep(args) if rank == 0 else 0
+    if args.workload == "fastx":
+        return run_fastx(args) if rank == 0 else 0
     if world > 1:
         import torch
         import torch.distributed as dist
