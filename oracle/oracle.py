@@ -50,6 +50,8 @@ def _load():
         lib.oracle_create.argtypes = [I, I, I, I, I, I, U64]
         lib.oracle_create_layout.restype = P
         lib.oracle_create_layout.argtypes = [I, I, I, I, I, I, U64, I]
+        lib.oracle_create_full.restype = P
+        lib.oracle_create_full.argtypes = [I, I, I, I, I, I, U64, I, I]
         lib.oracle_destroy.argtypes = [P]
         lib.oracle_destroy.restype = None
         lib.oracle_num_shards.argtypes = [P]
@@ -93,13 +95,21 @@ def _ptr(a: np.ndarray):
 class OracleSBF:
     """Plain CPU Super Bloom filter with the library's parameter domain."""
 
+    ALPHABETS = {"dna": 0, "protein": 1, "dna_triplet": 2}
+    SYMBOL_BYTES = {0: 1, 1: 1, 2: 3}
+
     def __init__(self, k: int, m: int, s: int, H: int, bits: int, shard_bits: int = 512,
-                 canonical: bool = True, layout: int = 0):
+                 canonical: bool = True, layout: int = 0, alphabet: int = 0):
         lib = _load()
-        h = lib.oracle_create_layout(k, m, s, H, shard_bits, 1 if canonical else 0, bits, layout)
+        alphabet = self.ALPHABETS.get(alphabet, alphabet)
+        h = lib.oracle_create_full(k, m, s, H, shard_bits, 1 if canonical else 0, bits, layout,
+                                   alphabet)
         if not h:
             raise ValueError(f"invalid oracle parameters k={k} m={m} s={s} H={H} "
-                             f"shard_bits={shard_bits} bits={bits} layout={layout}")
+                             f"shard_bits={shard_bits} bits={bits} layout={layout} "
+                             f"alphabet={alphabet} canonical={canonical}")
+        self.alphabet = alphabet
+        self.symbol_bytes = self.SYMBOL_BYTES[alphabet]
         self._h = ctypes.c_void_p(h)
         self._lib = lib
         self.k, self.m, self.s, self.H = k, m, s, H
@@ -166,7 +176,7 @@ class OracleSBF:
     def kmer_info(self, kmer) -> tuple[int, int]:
         """(minimizer value, shard) of one k-mer given as k bytes."""
         x = _u8(kmer)
-        assert x.size == self.k
+        assert x.size == self.k * self.symbol_bytes
         mu = ctypes.c_uint64(0)
         sh = ctypes.c_uint64(0)
         self._lib.oracle_kmer_info(self._h, _ptr(x), ctypes.byref(mu), ctypes.byref(sh))

@@ -44,6 +44,14 @@
  *              (Findere rule; Contains of Alg. 2).
  *   valid:     a k-mer is valid iff its k bytes lie in one read and all are
  *              A/C/G/T (Sec. IV-C validity, Sec. IV-F separators).
+ *   alphabets (Sec. IV-A: DNA 2 bits, protein 26 symbols in 5 bits, DNA
+ *              triplets 64 symbols in 6 bits over 3 bytes): a symbol is one
+ *              byte (DNA, protein: A..Z either case -> 0..25) or three
+ *              (triplet: 16 c0 + 4 c1 + c2 of three DNA codes); the packed
+ *              value, the sub-windows and the order key's width (32-bit when
+ *              m symbols fit 32 bits) use the symbol width; a read's k-mers
+ *              start at its first byte and then every symbol; the answer bit
+ *              is the k-mer's first byte; non-DNA alphabets are forward only.
  */
 #include "sbf_oracle.h"
 
@@ -59,6 +67,9 @@
 
 struct oracle_sbf {
   int k, m, s, H, B, canonical, layout;
+  int alphabet;   /* 0 DNA, 1 protein, 2 DNA triplets */
+  int sym_bits;   /* 2, 5, 6 */
+  int sym_bytes;  /* 1, 1, 3 */
   uint64_t N;      /* shards */
   uint64_t words;  /* 64-bit words = N * B / 64 */
   uint64_t* bits;
@@ -74,30 +85,48 @@ static int base_code(uint8_t ch) {
   }
 }
 
-static uint64_t len_mask(int len) { return len >= 32 ? ~0ULL : ((1ULL << (2 * len)) - 1ULL); }
+/* Mask of the low `nbits` bits. */
+static uint64_t bit_mask(int nbits) { return nbits >= 64 ? ~0ULL : ((1ULL << nbits) - 1ULL); }
 
-/* PackKmer: shift-and-OR, first base most significant. */
-static uint64_t pack_forward(const uint8_t* x, int len) {
+/* Code of the symbol starting at x, or -1 if it is not in the alphabet. */
+static int symbol_code(const oracle_sbf* f, const uint8_t* x) {
+  if (f->alphabet == 1) {
+    if (x[0] >= 'A' && x[0] <= 'Z') return x[0] - 'A';
+    if (x[0] >= 'a' && x[0] <= 'z') return x[0] - 'a';
+    return -1;
+  }
+  if (f->alphabet == 2) {
+    int a = base_code(x[0]), b = base_code(x[1]), c = base_code(x[2]);
+    if (a < 0 || b < 0 || c < 0) return -1;
+    return 16 * a + 4 * b + c;
+  }
+  return base_code(x[0]);
+}
+
+/* PackKmer: shift-and-OR, first symbol most significant. */
+static uint64_t pack_forward(const oracle_sbf* f, const uint8_t* x, int len) {
   uint64_t v = 0;
-  for (int i = 0; i < len; ++i) v = (v << 2) | (uint64_t)base_code(x[i]);
+  for (int i = 0; i < len; ++i)
+    v = (v << f->sym_bits) | (uint64_t)symbol_code(f, x + (size_t)i * (size_t)f->sym_bytes);
   return v;
 }
 
-/* Packed value of the reverse complement of x[0..len). */
-static uint64_t pack_revcomp(const uint8_t* x, int len) {
+/* Packed value of the reverse complement of x[0..len) (DNA only). */
+static uint64_t pack_revcomp(const oracle_sbf* f, const uint8_t* x, int len) {
+  if (f->alphabet != 0) return 0;
   uint64_t v = 0;
   for (int i = len - 1; i >= 0; --i) v = (v << 2) | (uint64_t)(3 - base_code(x[i]));
   return v;
 }
 
-/* Subwindow(packed, i, len) of Alg. 1: the len-mer at bases [i, i+len). */
-static uint64_t subwindow(uint64_t packed, int k, int i, int len) {
-  return (packed >> (2 * (k - len - i))) & len_mask(len);
+/* Subwindow(packed, i, len) of Alg. 1: the len-mer at symbols [i, i+len). */
+static uint64_t subwindow(const oracle_sbf* f, uint64_t packed, int i, int len) {
+  return (packed >> (f->sym_bits * (f->k - len - i))) & bit_mask(f->sym_bits * len);
 }
 
 /* Reverse complement of bases [i, i+len), read off the reverse-complemented k-mer. */
 static uint64_t subwindow_rc(uint64_t packed_rc, int i, int len) {
-  return (packed_rc >> (2 * i)) & len_mask(len);
+  return (packed_rc >> (2 * i)) & bit_mask(2 * len);
 }
 
 static uint64_t canonical_of(const oracle_sbf* f, uint64_t fwd, uint64_t rc) {
@@ -105,8 +134,8 @@ static uint64_t canonical_of(const oracle_sbf* f, uint64_t fwd, uint64_t rc) {
   return fwd < rc ? fwd : rc;
 }
 
-static uint64_t order_key(uint64_t v, int m) {
-  if (2 * m <= 32) return (uint64_t)((uint32_t)v * ORACLE_GOLDEN32);
+static uint64_t order_key(uint64_t v, int m_bits) {
+  if (m_bits <= 32) return (uint64_t)((uint32_t)v * ORACLE_GOLDEN32);
   return v * ORACLE_GOLDEN64;
 }
 
@@ -119,10 +148,10 @@ static uint64_t mix64(uint64_t x) {
   return x;
 }
 
-static uint64_t order_key(uint64_t v, int m);
+static uint64_t order_key(uint64_t v, int m_bits);
 
 static uint64_t shard_of(const oracle_sbf* f, uint64_t mu) {
-  if (f->layout == 1) return order_key(mu, f->m) & (f->N - 1);  /* minHash & (NumShards - 1) */
+  if (f->layout == 1) return order_key(mu, f->m * f->sym_bits) & (f->N - 1);  /* minHash & (NumShards - 1) */
   unsigned __int128 prod = (unsigned __int128)mix64(mu ^ ORACLE_SHARD_KEY) * f->N;
   return (uint64_t)(prod >> 64);
 }
@@ -162,8 +191,8 @@ static uint64_t bit_in_shard(const oracle_sbf* f, uint64_t h, int i) {
 static uint64_t minimizer(const oracle_sbf* f, uint64_t fwd, uint64_t rc) {
   uint64_t best_key = 0, mu = 0;
   for (int i = 0; i <= f->k - f->m; ++i) {
-    uint64_t v = canonical_of(f, subwindow(fwd, f->k, i, f->m), subwindow_rc(rc, i, f->m));
-    uint64_t key = order_key(v, f->m);
+    uint64_t v = canonical_of(f, subwindow(f, fwd, i, f->m), subwindow_rc(rc, i, f->m));
+    uint64_t key = order_key(v, f->m * f->sym_bits);
     if (i == 0 || key < best_key) {
       best_key = key;
       mu = v;
@@ -173,13 +202,13 @@ static uint64_t minimizer(const oracle_sbf* f, uint64_t fwd, uint64_t rc) {
 }
 
 static uint64_t smer_hash(const oracle_sbf* f, uint64_t fwd, uint64_t rc, int t) {
-  uint64_t v = canonical_of(f, subwindow(fwd, f->k, t, f->s), subwindow_rc(rc, t, f->s));
+  uint64_t v = canonical_of(f, subwindow(f, fwd, t, f->s), subwindow_rc(rc, t, f->s));
   return mix64(v ^ ORACLE_SMER_KEY);
 }
 
 static void insert_kmer(oracle_sbf* f, const uint8_t* x) {
-  uint64_t fwd = pack_forward(x, f->k);
-  uint64_t rc = pack_revcomp(x, f->k);
+  uint64_t fwd = pack_forward(f, x, f->k);
+  uint64_t rc = pack_revcomp(f, x, f->k);
   uint64_t shard = shard_of(f, minimizer(f, fwd, rc));
   for (int t = 0; t <= f->k - f->s; ++t) {
     uint64_t h = smer_hash(f, fwd, rc, t);
@@ -191,8 +220,8 @@ static void insert_kmer(oracle_sbf* f, const uint8_t* x) {
 }
 
 static int query_kmer(const oracle_sbf* f, const uint8_t* x) {
-  uint64_t fwd = pack_forward(x, f->k);
-  uint64_t rc = pack_revcomp(x, f->k);
+  uint64_t fwd = pack_forward(f, x, f->k);
+  uint64_t rc = pack_revcomp(f, x, f->k);
   uint64_t shard = shard_of(f, minimizer(f, fwd, rc));
   for (int t = 0; t <= f->k - f->s; ++t) {
     uint64_t h = smer_hash(f, fwd, rc, t);
@@ -204,11 +233,15 @@ static int query_kmer(const oracle_sbf* f, const uint8_t* x) {
   return 1;
 }
 
-/* A k-mer starting at p is valid iff it ends inside its read and has only ACGT. */
+/* Bytes of a k-mer. */
+static uint64_t kmer_bytes(const oracle_sbf* f) { return (uint64_t)f->k * (uint64_t)f->sym_bytes; }
+
+/* A k-mer starting at p is valid iff it ends inside its read and all its
+ * symbols are in the alphabet. */
 static int kmer_valid(const oracle_sbf* f, const uint8_t* seq, uint64_t p, uint64_t read_end) {
-  if (p + (uint64_t)f->k > read_end) return 0;
+  if (p + kmer_bytes(f) > read_end) return 0;
   for (int i = 0; i < f->k; ++i)
-    if (base_code(seq[p + (uint64_t)i]) < 0) return 0;
+    if (symbol_code(f, seq + p + (uint64_t)i * (uint64_t)f->sym_bytes) < 0) return 0;
   return 1;
 }
 
@@ -219,6 +252,15 @@ oracle_sbf* oracle_create(int k, int m, int s, int H, int shard_bits, int canoni
 
 oracle_sbf* oracle_create_layout(int k, int m, int s, int H, int shard_bits, int canonical,
                                  uint64_t bits, int layout) {
+  return oracle_create_full(k, m, s, H, shard_bits, canonical, bits, layout, 0);
+}
+
+oracle_sbf* oracle_create_full(int k, int m, int s, int H, int shard_bits, int canonical,
+                               uint64_t bits, int layout, int alphabet) {
+  static const int sym_bits[3] = {2, 5, 6}, sym_bytes[3] = {1, 1, 3};
+  if (alphabet < 0 || alphabet > 2) return NULL;
+  if (alphabet != 0 && canonical) return NULL;               /* no reverse complement */
+  if (k * sym_bits[alphabet] > 64) return NULL;              /* one 64-bit packed k-mer */
   if (layout != 0 && layout != 1) return NULL;
   if (layout == 1 && shard_bits != 256) return NULL;
   if (k < 1 || k > 32 || m < 1 || m > k || s < 1 || s > k || H < 1 || H > 16) return NULL;
@@ -228,6 +270,9 @@ oracle_sbf* oracle_create_layout(int k, int m, int s, int H, int shard_bits, int
   if (!f) return NULL;
   f->k = k; f->m = m; f->s = s; f->H = H; f->B = shard_bits; f->canonical = canonical ? 1 : 0;
   f->layout = layout;
+  f->alphabet = alphabet;
+  f->sym_bits = sym_bits[alphabet];
+  f->sym_bytes = sym_bytes[alphabet];
   f->N = (bits + (uint64_t)shard_bits - 1) / (uint64_t)shard_bits;
   if (layout == 1) { /* round the shard count up to a power of two */
     uint64_t n = 1;
@@ -257,7 +302,7 @@ void oracle_insert(oracle_sbf* f, const uint8_t* seq, uint64_t seq_len, const ui
                    uint64_t n_reads) {
   (void)seq_len;
   for (uint64_t r = 0; r < n_reads; ++r)
-    for (uint64_t p = off[r]; p + (uint64_t)f->k <= off[r + 1]; ++p)
+    for (uint64_t p = off[r]; p + kmer_bytes(f) <= off[r + 1]; p += (uint64_t)f->sym_bytes)
       if (kmer_valid(f, seq, p, off[r + 1])) insert_kmer(f, seq + p);
 }
 
@@ -266,7 +311,7 @@ void oracle_query(const oracle_sbf* f, const uint8_t* seq, uint64_t seq_len, con
   if (out_bits) memset(out_bits, 0, ((seq_len + 31) / 32) * sizeof(uint32_t));
   for (uint64_t r = 0; r < n_reads; ++r) {
     uint32_t hits = 0;
-    for (uint64_t p = off[r]; p + (uint64_t)f->k <= off[r + 1]; ++p) {
+    for (uint64_t p = off[r]; p + kmer_bytes(f) <= off[r + 1]; p += (uint64_t)f->sym_bytes) {
       if (kmer_valid(f, seq, p, off[r + 1]) && query_kmer(f, seq + p)) {
         ++hits;
         if (out_bits) out_bits[p >> 5] |= 1U << (p & 31);
@@ -295,6 +340,7 @@ void oracle_query_positions(const oracle_sbf* f, const uint8_t* seq, uint64_t se
     if (p >= seq_len || n_reads == 0) continue;
     uint64_t r = read_of(off, n_reads, p);
     if (p < off[r] || p >= off[r + 1]) continue;
+    if ((p - off[r]) % (uint64_t)f->sym_bytes != 0) continue;  /* not a symbol start */
     if (kmer_valid(f, seq, p, off[r + 1])) out[i] = (uint8_t)query_kmer(f, seq + p);
   }
 }
@@ -307,12 +353,12 @@ void oracle_count_runs(const oracle_sbf* f, const uint8_t* seq, uint64_t seq_len
   for (uint64_t r = 0; r < n_reads; ++r) {
     int have_prev = 0;
     uint64_t prev_mu = 0;
-    for (uint64_t p = off[r]; p + (uint64_t)f->k <= off[r + 1]; ++p) {
+    for (uint64_t p = off[r]; p + kmer_bytes(f) <= off[r + 1]; p += (uint64_t)f->sym_bytes) {
       if (!kmer_valid(f, seq, p, off[r + 1])) {
         have_prev = 0;
         continue;
       }
-      uint64_t mu = minimizer(f, pack_forward(seq + p, f->k), pack_revcomp(seq + p, f->k));
+      uint64_t mu = minimizer(f, pack_forward(f, seq + p, f->k), pack_revcomp(f, seq + p, f->k));
       ++valid;
       if (!have_prev || mu != prev_mu) ++runs;
       have_prev = 1;
@@ -325,7 +371,7 @@ void oracle_count_runs(const oracle_sbf* f, const uint8_t* seq, uint64_t seq_len
 
 void oracle_kmer_info(const oracle_sbf* f, const uint8_t* x, uint64_t* out_minimizer,
                       uint64_t* out_shard) {
-  uint64_t mu = minimizer(f, pack_forward(x, f->k), pack_revcomp(x, f->k));
+  uint64_t mu = minimizer(f, pack_forward(f, x, f->k), pack_revcomp(f, x, f->k));
   *out_minimizer = mu;
   *out_shard = shard_of(f, mu);
 }

@@ -36,6 +36,12 @@ oracle_sbf* oracle_create(int k, int m, int s, int H, int shard_bits, int canoni
  * = minimizer order key & (N - 1), hash i in 64-bit word i mod 4). */
 oracle_sbf* oracle_create_layout(int k, int m, int s, int H, int shard_bits, int canonical,
                                  uint64_t bits, int layout);
+/* alphabet 0: DNA (2-bit symbols, one byte each, the default); 1: protein
+ * (A..Z either case, 5-bit symbols); 2: DNA triplets (three DNA bytes per
+ * 6-bit symbol; a read's k-mers start at its first byte and every third
+ * byte after).  Non-DNA alphabets need canonical = 0 and k * bits <= 64. */
+oracle_sbf* oracle_create_full(int k, int m, int s, int H, int shard_bits, int canonical,
+                               uint64_t bits, int layout, int alphabet);
 void oracle_destroy(oracle_sbf* f);
 
 uint64_t oracle_num_shards(const oracle_sbf* f);

@@ -466,3 +466,129 @@ def test_oracle_regression_digests():
     spec.loader.exec_module(mod)
     stored = _golden("oracle_regression.json")["cases"]
     assert mod.compute() == stored
+
+
+# ---------------------------------------------------------------------------
+# other alphabets (Sec. IV-A): protein (26 symbols, 5 bits) and DNA triplets
+# (64 symbols, 6 bits, three bytes each)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("alphabet,kmer,expected", [
+    ("protein", "ACD", 0 * 1024 + 2 * 32 + 3),     # A=0, C=2, D=3 in 5-bit digits
+    ("protein", "acd", 0 * 1024 + 2 * 32 + 3),     # either case
+    ("protein", "ZZZ", 25 * 1024 + 25 * 32 + 25),
+    ("dna_triplet", "AAAACG", 0 * 64 + 6),         # AAA = 0, ACG = 16*0 + 4*1 + 2
+    ("dna_triplet", "TTTTTT", 63 * 64 + 63),
+])
+def test_alphabet_packing_closed_form(alphabet, kmer, expected):
+    k = 3 if alphabet == "protein" else 2
+    f = OracleSBF(k, k, k, 1, 512, canonical=False, alphabet=alphabet)
+    mu, _ = f.kmer_info(np.frombuffer(kmer.encode(), dtype=np.uint8))
+    assert mu == expected
+
+
+def _protein_reads(rng, k):
+    letters = "ACDEFGHIKLMNPQRSTVWYXBZUOJ"
+    reads = ["".join(rng.choice(letters) for _ in range(rng.randint(0, 4 * k))) for _ in range(12)]
+    reads.append("".join(rng.choice(letters + "*-.1") for _ in range(3 * k)))  # invalid symbols
+    reads.append("".join(rng.choice(letters) for _ in range(k - 1)))           # shorter than k
+    reads.append("")
+    reads.append("".join(rng.choice(letters) for _ in range(2 * k)).lower())
+    reads.append("W" * (3 * k))
+    return reads
+
+
+def _triplet_reads(rng, k):
+    reads = [_random_dna(rng, rng.randint(0, 12 * k)) for _ in range(12)]  # lengths not multiples of 3
+    reads.append(_random_dna(rng, 9 * k, "ACGTN"))
+    reads.append(_random_dna(rng, 3 * k - 1))                               # one byte short
+    reads.append("")
+    reads.append(_random_dna(rng, 6 * k).lower())
+    return reads
+
+
+ALPHA_CONFIGS = [
+    # k, m, s, H, bits, B, layout, alphabet
+    (12, 6, 10, 4, 1 << 15, 512, 0, 1),
+    (12, 7, 12, 1, 1 << 14, 512, 0, 1),    # s = k; 35-bit m-mers: 64-bit key
+    (10, 4, 8, 8, 1 << 15, 256, 0, 1),
+    (12, 6, 9, 16, 1 << 15, 512, 0, 1),    # salted multiply
+    (12, 6, 10, 4, 1 << 15, 256, 1, 1),    # the paper's layout
+    (10, 5, 8, 4, 1 << 15, 512, 0, 2),
+    (10, 6, 10, 2, 1 << 14, 512, 0, 2),    # 36-bit m-mers: 64-bit key
+    (8, 4, 6, 4, 1 << 14, 256, 1, 2),
+]
+
+
+@pytest.mark.parametrize("cfg", ALPHA_CONFIGS, ids=lambda c: "_".join(map(str, c)))
+def test_alphabet_bruteforce_filter_and_answers(cfg):
+    k, m, s, H, bits, B, layout, alphabet = cfg
+    rng = random.Random(hash(cfg) & 0xFFFF)
+    reads = _protein_reads(rng, k) if alphabet == 1 else _triplet_reads(rng, k)
+    seq, off = _reads_to_arrays(reads)
+    f = OracleSBF(k, m, s, H, bits, shard_bits=B, canonical=False, layout=layout, alphabet=alphabet)
+    f.insert(seq, off)
+    b = BruteSBF(k, m, s, H, bits, shard_bits=B, canonical=False, layout=layout, alphabet=alphabet)
+    for r in reads:
+        b.insert_read(r)
+    assert np.array_equal(f.words(), b.words())
+    # queries: the reads, one-symbol mutants, shifted copies and random reads
+    qreads = list(reads)
+    for r in reads:
+        if len(r) > 3:
+            i = rng.randrange(len(r))
+            qreads.append(r[:i] + rng.choice("ACGT") + r[i + 1:])
+            qreads.append(r[1:])  # a triplet read out of frame
+    qreads += (_protein_reads(rng, k) if alphabet == 1 else _triplet_reads(rng, k))
+    qseq, qoff = _reads_to_arrays(qreads)
+    bits_out, hits = f.query(qseq, qoff)
+    bitset = b.bitset()
+    for ri, r in enumerate(qreads):
+        want = {p: int(b.query_kmer(km, bitset)) for p, km in b.kmers_of(r)}
+        for p in range(len(r)):
+            gp = int(qoff[ri]) + p
+            got = (int(bits_out[gp >> 5]) >> (gp & 31)) & 1
+            assert got == want.get(p, 0), (cfg, ri, p)
+        assert hits[ri] == sum(want.values())
+    # every inserted k-mer is positive (no false negatives)
+    _, ih = f.query(seq, off)
+    assert [int(x) for x in ih] == [sum(1 for _ in b.kmers_of(r)) for r in reads]
+
+
+def test_triplet_frame_and_valid_counts():
+    """Triplet k-mers start at a read's first byte and every third byte after
+    (Sec. IV-A multi-byte symbols): runs counted by the oracle match the
+    string-level reading frame."""
+    rng = random.Random(5)
+    reads = [_random_dna(rng, n) for n in (29, 30, 31, 32, 90, 91, 92, 300)]
+    seq, off = _reads_to_arrays(reads)
+    f = OracleSBF(10, 5, 8, 4, 1 << 16, canonical=False, alphabet="dna_triplet")
+    b = BruteSBF(10, 5, 8, 4, 1 << 16, canonical=False, alphabet=2)
+    valid, _ = f.count_runs(seq, off)
+    assert valid == sum(max(0, len(r) // 3 - 10 + 1) for r in reads)
+    assert valid == sum(1 for r in reads for _ in b.kmers_of(r))
+    f.insert(seq, off)
+    bits_out, hits = f.query(seq, off)
+    for ri, r in enumerate(reads):
+        for p in range(len(r)):
+            gp = int(off[ri]) + p
+            bit = (int(bits_out[gp >> 5]) >> (gp & 31)) & 1
+            assert bit == int(p % 3 == 0 and p + 30 <= len(r)), (ri, p)
+
+
+def test_protein_fpr_matches_conditional_closed_form():
+    """Eq. 2 made shard-aware holds for 5-bit symbols: random aliens against a
+    filter built from a random 'proteome'."""
+    from paper_2606_24417_gb300 import synth as sy
+
+    letters = np.frombuffer(b"ACDEFGHIKLMNPQRSTVWY", dtype=np.uint8)
+    prot = letters[sy.randint(8, 1, 400_000, 0, 20)]
+    f = OracleSBF(12, 6, 10, 4, 1 << 21, canonical=False, alphabet="protein")
+    f.insert(prot, np.array([0, prot.size], dtype=np.uint64))
+    p_hat = conditional_fpr(f.words(), 12, 10, 4, 512)
+    Q = 300_000
+    q = letters[sy.randint(9, 1, Q * 12, 0, 20)]
+    qoff = np.arange(0, Q * 12 + 1, 12, dtype=np.uint64)
+    _, hits = f.query(q, qoff)
+    X = int(hits.sum())
+    assert p_hat > 1e-4
+    assert binomial_two_sided_p(X, Q, p_hat) > 1e-4, (X, Q * p_hat)
