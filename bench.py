@@ -951,6 +951,138 @@ def run_fastx(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# the other alphabets of Sec. IV-A on the generic kernels
+# ---------------------------------------------------------------------------
+def run_alphabets(args):
+    """Protein filter (k=12, m=6, s=10, H=4 over 5-bit residues) on a 100M-
+    residue synthetic proteome, and a DNA-triplet filter (k=10, m=5, s=8,
+    H=4 over 6-bit codons) on the 100 Mbp genome read as codons; each queried
+    with 1M sampled reads (1% substitutions) + 1M random reads."""
+    import torch
+
+    from paper_2606_24417_gb300 import build_lib, synth
+    from paper_2606_24417_gb300.sbf import SuperBloomFilter
+
+    build_lib.build()
+    torch.cuda.set_device(0)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    n_s = n_r = 1_000_000
+    out = {}
+    cases = {
+        "protein": dict(k=12, m=6, s=10, H=4, bits=1 << 31, alphabet="protein", sym=1),
+        "dna_triplet": dict(k=10, m=5, s=8, H=4, bits=1 << 29, alphabet="dna_triplet", sym=3),
+    }
+    for name, c in cases.items():
+        if name == "protein":
+            ref = synth.protein_sequence(100_000_000, 7)
+            q1, o1 = synth.sample_peptides(ref, n_s, 150, 0.01, 8)
+            q2, o2 = synth.random_peptides(n_r, 150, 9)
+            rlen = 150
+        else:
+            ref = synth.bacterial_genome(GENOME_BP, seed=2)
+            q1, o1 = synth.sample_reads(ref, n_s, 450, 0.01, 8)
+            q2, o2 = synth.random_reads(n_r, 450, 9)
+            rlen = 450
+        q = np.concatenate([q1, q2])
+        qo = np.concatenate([o1, o2[1:] + o1[-1]]).astype(np.uint64)
+        ins_kmers = ref.size // c["sym"] - c["k"] + 1
+        q_kmers = (n_s + n_r) * (rlen // c["sym"] - c["k"] + 1)
+        f = SuperBloomFilter(c["k"], c["m"], c["s"], c["H"], c["bits"], shard_bits=512,
+                             canonical=False, alphabet=c["alphabet"])
+        dr, dro = dev(ref), dev(np.array([0, ref.size], dtype=np.int64))
+        dq, dqo = dev(q), dev(qo.astype(np.int64))
+        hits = torch.empty(n_s + n_r, dtype=torch.int32, device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ti, tq = [], []
+        for rep in range(args.warmup + args.steps):
+            f.clear()
+            ev[0].record()
+            f.insert(dr, dro)
+            ev[1].record()
+            f.query(dq, dqo, hits=hits, want_bits=False)
+            ev[2].record()
+            torch.cuda.synchronize()
+            if rep >= args.warmup:
+                ti.append(ev[0].elapsed_time(ev[1]))
+                tq.append(ev[1].elapsed_time(ev[2]))
+        h = hits.cpu().numpy()
+        out[name] = {"k": c["k"], "m": c["m"], "s": c["s"], "H": c["H"], "filter_bits": c["bits"],
+                     "insert_kmers": ins_kmers, "query_kmers": q_kmers,
+                     "insert_ms": statistics.median(ti), "query_ms": statistics.median(tq),
+                     "insert_kmers_per_s": ins_kmers / (statistics.median(ti) / 1e3),
+                     "query_kmers_per_s": q_kmers / (statistics.median(tq) / 1e3),
+                     "sampled_hit_fraction": float(h[:n_s].sum()) / (n_s * (rlen // c["sym"] - c["k"] + 1)),
+                     "fpr_random": float(h[n_s:].sum()) / (n_r * (rlen // c["sym"] - c["k"] + 1)),
+                     "kernel": "generic" if not f.fused else "fused"}
+        f.close()
+    print(json.dumps({"workload": "alphabets: protein filter on a 100M-residue synthetic proteome "
+                      "(150-residue peptides) and DNA-triplet filter on the 100 Mbp genome "
+                      "(450 bp reads); 1M sampled (1% substitutions) + 1M random queries each",
+                      "results": out}), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# false positives against filter size (Sec. V-D, Fig. 7)
+# ---------------------------------------------------------------------------
+def run_fpr_curve(args):
+    """Insert the 100 Mbp genome (stand-in for C. elegans) into filters of
+    2^22 .. 2^39 bits for s in {28, 30, 31} (k=31, m=16, H=4, 512-bit shards)
+    and count false positives among 10^9 independent random 31-mers (reads of
+    exactly 31 bases, resident on the device).  Beside each count: the
+    shard-aware closed form (Eq. 2 conditioned on the built filter) where the
+    filter is small enough to copy to the host."""
+    import torch
+
+    from paper_2606_24417_gb300 import build_lib, synth
+    from paper_2606_24417_gb300.sbf import SuperBloomFilter
+    from paper_2606_24417_gb300.stats import expected_fpr
+
+    build_lib.build()
+    torch.cuda.set_device(0)
+    n_alien = 1_000_000_000
+    batch = 100_000_000
+    genome = synth.bacterial_genome(GENOME_BP, seed=2)
+    dg = torch.from_numpy(genome).cuda()
+    dgo = torch.tensor([0, genome.size], dtype=torch.int64).cuda()
+    t = time.time()
+    aliens = []
+    for b in range(n_alien // batch):
+        a = synth.uniform_dna(batch * K, 1000 + b)
+        aliens.append(torch.from_numpy(a).cuda())
+    aoff = torch.arange(0, batch * K + 1, K, dtype=torch.int64, device="cuda")
+    hits = torch.empty(batch, dtype=torch.int32, device="cuda")
+    log(f"[bench] 10^9 random 31-mers on the device in {time.time() - t:.1f}s")
+    rows = []
+    for s_ in (28, 30, 31):
+        for e in range(22, 40):
+            f = SuperBloomFilter(K, M, s_, H, 1 << e, shard_bits=SHARD_BITS)
+            f.insert(dg, dgo)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fp = 0
+            for a in aliens:
+                f.query(a, aoff, hits=hits, want_bits=False)
+                fp += int(hits.sum().item())
+            dt = time.perf_counter() - t0
+            row = {"s": s_, "log2_bits": e, "false_positives": fp, "fpr": fp / n_alien,
+                   "query_seconds": dt}
+            if e <= 34:
+                row["fpr_expected"] = expected_fpr(f.words(), K, s_, H, SHARD_BITS)
+            rows.append(row)
+            log(f"[bench] s={s_} 2^{e}: {fp} false positives")
+            f.close()
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    with open(os.path.join(ROOT, "gpurun_out", "fpr_curve.json"), "w") as fh:
+        json.dump(rows, fh)
+    print(json.dumps({"workload": "fpr_curve: 100 Mbp bacterial-shaped genome inserted into "
+                      "2^22..2^39-bit filters (k=31, m=16, H=4, 512-bit shards), s in {28,30,31}; "
+                      "false positives among 10^9 independent random 31-mers",
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -960,7 +1092,8 @@ def main():
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: 2M query reads (300 MB, still larger than L2) for profiling")
     ap.add_argument("--workload", default="bacterial",
-                    choices=["bacterial", "batched", "served", "sweep", "paper_sweep", "fastx"],
+                    choices=["bacterial", "batched", "served", "sweep", "paper_sweep", "fastx",
+                             "alphabets", "fpr_curve"],
                     help="batched: the many-filter workload (its own JSON line)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="device-timed steps only (no e2e, no CPU baseline): profiling runs")
@@ -983,6 +1116,10 @@ def main():
         return run_paper_sweep(args) if rank == 0 else 0
     if args.workload == "fastx":
         return run_fastx(args) if rank == 0 else 0
+    if args.workload == "alphabets":
+        return run_alphabets(args) if rank == 0 else 0
+    if args.workload == "fpr_curve":
+        return run_fpr_curve(args) if rank == 0 else 0
     if world > 1:
         import torch
         import torch.distributed as dist

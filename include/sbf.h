@@ -99,6 +99,25 @@ int sbf_create_layout(int k, int m, int s, int H, uint64_t bits, int shard_bits,
                       int layout, sbf_filter** out);
 /* The filter's layout (SBF_LAYOUT_*), or SBF_EINVAL for NULL. */
 int sbf_layout(const sbf_filter* f);
+
+/* Alphabets (Sec. IV-A).  SBF_ALPHABET_DNA: the 2-bit bases above.
+ * SBF_ALPHABET_PROTEIN: 26 symbols A..Z (either case) -> 0..25 in 5 bits,
+ * one byte each; any other byte is invalid.  SBF_ALPHABET_DNA_TRIPLET: 64
+ * symbols of three DNA bytes each (16 c0 + 4 c1 + c2, 6 bits); a triplet with
+ * a non-ACGT byte is invalid, and a read's k-mers start at its first byte and
+ * every third byte after (a trailing partial triplet is ignored).  For both:
+ * k symbols are packed first-symbol-most-significant into 64 bits (k * bits
+ * <= 64: k <= 12 for protein, k <= 10 for triplets), the order key is 32-bit
+ * when m symbols fit 32 bits, k-mers are forward only (canonical must be 0),
+ * and a query's answer bit is the k-mer's first byte.  Hashes and layouts are
+ * those of the DNA filter.  These filters use the generic kernels (batches
+ * and the server need the fused DNA kernels).  sbf_create_layout is
+ * sbf_create_full with SBF_ALPHABET_DNA. */
+enum { SBF_ALPHABET_DNA = 0, SBF_ALPHABET_PROTEIN = 1, SBF_ALPHABET_DNA_TRIPLET = 2 };
+int sbf_create_full(int k, int m, int s, int H, uint64_t bits, int shard_bits, int canonical,
+                    int layout, int alphabet, sbf_filter** out);
+/* The filter's alphabet (SBF_ALPHABET_*), or SBF_EINVAL for NULL. */
+int sbf_alphabet(const sbf_filter* f);
 /* Frees the device memory.  NULL is a no-op.  Must not be called while work
  * on the filter is in flight. */
 void sbf_destroy(sbf_filter* f);

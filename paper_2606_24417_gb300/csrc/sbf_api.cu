@@ -106,13 +106,22 @@ extern "C" {
 
 const char* sbf_last_error(void) { return g_err; }
 
-int sbf_create_layout(int k, int m, int s, int H, uint64_t bits, int shard_bits, int canonical,
-                      int layout, sbf_filter** out) {
+int sbf_create_full(int k, int m, int s, int H, uint64_t bits, int shard_bits, int canonical,
+                    int layout, int alphabet, sbf_filter** out) {
   clear_error();
   if (!out) return fail(SBF_EINVAL, "out is NULL");
   *out = nullptr;
   int rc = check_params(k, m, s, H, bits, shard_bits);
   if (rc != SBF_OK) return rc;
+  if (alphabet != SBF_ALPHABET_DNA && alphabet != SBF_ALPHABET_PROTEIN &&
+      alphabet != SBF_ALPHABET_DNA_TRIPLET)
+    return fail(SBF_EINVAL, "alphabet must be 0, 1 or 2 (got %d)", alphabet);
+  if (alphabet != SBF_ALPHABET_DNA) {
+    const int sym_bits = alphabet == SBF_ALPHABET_PROTEIN ? 5 : 6;
+    if (canonical) return fail(SBF_EINVAL, "canonical k-mers need the DNA alphabet");
+    if (k * sym_bits > 64)
+      return fail(SBF_EINVAL, "k=%d symbols of %d bits exceed 64 bits", k, sym_bits);
+  }
   if (layout != SBF_LAYOUT_DEFAULT && layout != SBF_LAYOUT_PAPER)
     return fail(SBF_EINVAL, "layout must be 0 or 1 (got %d)", layout);
   if (layout == SBF_LAYOUT_PAPER && shard_bits != 256)
@@ -146,11 +155,16 @@ int sbf_create_layout(int k, int m, int s, int H, uint64_t bits, int shard_bits,
     delete f;
     return cuda_fail(e, "cudaMemset");
   }
-  f->geom = make_geom(words, n_shards, k, m, s, H, shard_bits, canonical ? 1 : 0, layout);
+  f->geom = make_geom(words, n_shards, k, m, s, H, shard_bits, canonical ? 1 : 0, layout, alphabet);
   f->n_words = n_words;
   f->fused = fused_supported(f->geom);
   *out = f;
   return SBF_OK;
+}
+
+int sbf_create_layout(int k, int m, int s, int H, uint64_t bits, int shard_bits, int canonical,
+                      int layout, sbf_filter** out) {
+  return sbf_create_full(k, m, s, H, bits, shard_bits, canonical, layout, SBF_ALPHABET_DNA, out);
 }
 
 int sbf_create_ex(int k, int m, int s, int H, uint64_t bits, int shard_bits, int canonical,
@@ -163,6 +177,8 @@ int sbf_create(int k, int m, int s, int H, uint64_t bits, sbf_filter** out) {
 }
 
 int sbf_layout(const sbf_filter* f) { return f ? f->geom.layout : SBF_EINVAL; }
+
+int sbf_alphabet(const sbf_filter* f) { return f ? f->geom.alphabet : SBF_EINVAL; }
 
 void sbf_destroy(sbf_filter* f) {
   if (!f) return;

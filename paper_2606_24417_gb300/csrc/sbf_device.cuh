@@ -33,6 +33,9 @@ struct Geom {
   int shard_bits;      // B
   int canonical;
   int layout;          // 0: this library's layout; 1: the paper's literal one
+  int alphabet;        // 0: DNA; 1: protein; 2: DNA triplets (Sec. IV-A)
+  int sym_bits;        // bits per symbol: 2, 5, 6
+  int sym_bytes;       // bytes per symbol: 1, 1, 3
   int sectors;         // S = largest power of two <= min(H, B/64); B/64 for layout 1
   int sector_bits;     // B / S
   int sector_log2;     // b = log2(B / S)
@@ -42,8 +45,13 @@ struct Geom {
 // Layout 1 is Sec. IV-B and Alg. 1/2 taken literally: 2^P shards (the caller
 // rounds N up), shard = minimizer order key & (N - 1), and every 64-bit word
 // is a sector (hash i in word i mod W; with H < W some words stay unused).
+// Alphabets (Sec. IV-A): DNA (A/C/G/T -> 0..3, 2 bits), protein (A..Z either
+// case -> 0..25, 5 bits), DNA triplets (three DNA bytes -> 16 c0 + 4 c1 + c2,
+// 6 bits).  Packing, sub-windows and the order key's width follow the symbol
+// width; a read's k-mers start at its first byte and every symbol after.
 __host__ __device__ inline Geom make_geom(uint64_t* words, uint64_t n_shards, int k, int m, int s,
-                                          int H, int shard_bits, int canonical, int layout = 0) {
+                                          int H, int shard_bits, int canonical, int layout = 0,
+                                          int alphabet = 0) {
   Geom g;
   g.words = words;
   g.n_shards = n_shards;
@@ -51,6 +59,9 @@ __host__ __device__ inline Geom make_geom(uint64_t* words, uint64_t n_shards, in
   g.shard_bits = shard_bits;
   g.canonical = canonical;
   g.layout = layout;
+  g.alphabet = alphabet;
+  g.sym_bits = alphabet == 1 ? 5 : alphabet == 2 ? 6 : 2;
+  g.sym_bytes = alphabet == 2 ? 3 : 1;
   int W = shard_bits / 64;
   int lim = H < W ? H : W;  // sectors: the largest power of two not above min(H, W)
   g.sectors = 1;
@@ -83,10 +94,10 @@ __device__ __forceinline__ bool base_valid(uint32_t ch) {
   return lc == 'a' || lc == 'c' || lc == 'g' || lc == 't';
 }
 
-// Minimizer order key of a canonical m-mer: bijective multiplicative hash in
-// the narrowest machine word holding 2m bits.
-__device__ __forceinline__ uint64_t order_key(uint64_t v, int m) {
-  return (2 * m <= 32) ? (uint64_t)((uint32_t)v * kGolden32) : v * kGolden64;
+// Minimizer order key of a canonical m-mer of m_bits bits: bijective
+// multiplicative hash in the narrowest machine word holding them.
+__device__ __forceinline__ uint64_t order_key(uint64_t v, int m_bits) {
+  return (m_bits <= 32) ? (uint64_t)((uint32_t)v * kGolden32) : v * kGolden64;
 }
 
 __device__ __forceinline__ uint64_t shard_of(uint64_t mu, uint64_t n_shards) {
@@ -95,7 +106,7 @@ __device__ __forceinline__ uint64_t shard_of(uint64_t mu, uint64_t n_shards) {
 
 // Shard of minimizer mu under either layout (layout 1: n_shards is 2^P).
 __device__ __forceinline__ uint64_t shard_of(const Geom& g, uint64_t mu) {
-  if (g.layout == 1) return order_key(mu, g.m) & (g.n_shards - 1);
+  if (g.layout == 1) return order_key(mu, g.m * g.sym_bits) & (g.n_shards - 1);
   return shard_of(mu, g.n_shards);
 }
 
@@ -115,6 +126,24 @@ __device__ __forceinline__ uint32_t bit_in_shard(const Geom& g, uint64_t h, int 
 
 __device__ __forceinline__ uint64_t len_mask(int len) {
   return len >= 32 ? ~0ull : ((1ull << (2 * len)) - 1ull);
+}
+
+__device__ __forceinline__ uint64_t bit_mask(int nbits) {
+  return nbits >= 64 ? ~0ull : ((1ull << nbits) - 1ull);
+}
+
+// Code of the symbol at x, or -1 if it is not in the alphabet.
+__device__ __forceinline__ int symbol_code(const Geom& g, const uint8_t* x) {
+  if (g.alphabet == 1) {
+    const uint32_t u = (uint32_t)(x[0] | 0x20u) - (uint32_t)'a';  // either case
+    const uint32_t c = x[0];
+    return (u < 26u && ((c >= 'A' && c <= 'Z') || (c >= 'a' && c <= 'z'))) ? (int)u : -1;
+  }
+  if (g.alphabet == 2) {
+    if (!base_valid(x[0]) || !base_valid(x[1]) || !base_valid(x[2])) return -1;
+    return (int)(16u * base_code(x[0]) + 4u * base_code(x[1]) + base_code(x[2]));
+  }
+  return base_valid(x[0]) ? (int)base_code(x[0]) : -1;
 }
 
 }  // namespace sbf

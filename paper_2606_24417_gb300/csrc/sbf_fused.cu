@@ -54,6 +54,7 @@ cudaError_t launch_params(const Params& P, bool insert, cudaStream_t st) { retur
 
 bool fused_supported(const Geom& g) {
   if (getenv("SBF_FORCE_GENERIC")) return false;
+  if (g.alphabet != 0) return false;  // the fused staging encodes 2-bit DNA
   if (g.k < 2 || g.k > 32) return false;
   if (g.s <= 16) return false;  // the s-mer extraction shifts by 64 - 2s < 32
   int w = fused::window_of(g);

@@ -24,6 +24,9 @@ struct KmerView {
   uint64_t fwd, rc;  // packed k-mer and its reverse complement
 };
 
+// The k-mer starting at byte p: valid iff p is a symbol start of its read
+// (read start + a multiple of the symbol bytes), it ends inside the read and
+// all k symbols are in the alphabet.
 __device__ __forceinline__ KmerView load_kmer(const Geom& g, const uint8_t* seq, uint64_t seq_len,
                                               const uint64_t* off, uint64_t n_reads, uint64_t p) {
   KmerView v{false, 0, 0, 0};
@@ -31,14 +34,15 @@ __device__ __forceinline__ KmerView load_kmer(const Geom& g, const uint8_t* seq,
   v.read = read_of(off, n_reads, p);
   uint64_t end = off[v.read + 1];
   if (end > seq_len) end = seq_len;
-  if (off[v.read] > p || p + (uint64_t)g.k > end) return v;
+  const uint64_t sb = (uint64_t)g.sym_bytes;
+  if (off[v.read] > p || p + (uint64_t)g.k * sb > end) return v;
+  if (sb > 1 && (p - off[v.read]) % sb != 0) return v;
   uint64_t fwd = 0, rc = 0;
   for (int i = 0; i < g.k; ++i) {
-    uint32_t ch = seq[p + i];
-    if (!base_valid(ch)) return v;
-    uint32_t c = base_code(ch);
-    fwd = (fwd << 2) | c;
-    rc |= (uint64_t)(3u - c) << (2 * i);
+    const int c = symbol_code(g, seq + p + (uint64_t)i * sb);
+    if (c < 0) return v;
+    fwd = (fwd << g.sym_bits) | (uint64_t)c;
+    if (g.alphabet == 0) rc |= (uint64_t)(3 - c) << (2 * i);
   }
   v.valid = true;
   v.fwd = fwd;
@@ -48,7 +52,7 @@ __device__ __forceinline__ KmerView load_kmer(const Geom& g, const uint8_t* seq,
 
 __device__ __forceinline__ uint64_t canon(const Geom& g, uint64_t fwd_packed, uint64_t rc_packed,
                                           int i, int len) {
-  uint64_t f = (fwd_packed >> (2 * (g.k - len - i))) & len_mask(len);
+  uint64_t f = (fwd_packed >> (g.sym_bits * (g.k - len - i))) & bit_mask(g.sym_bits * len);
   if (!g.canonical) return f;
   uint64_t r = (rc_packed >> (2 * i)) & len_mask(len);
   return f < r ? f : r;
@@ -58,7 +62,7 @@ __device__ __forceinline__ uint64_t minimizer(const Geom& g, uint64_t fwd, uint6
   uint64_t best = 0, mu = 0;
   for (int i = 0; i <= g.k - g.m; ++i) {
     uint64_t v = canon(g, fwd, rc, i, g.m);
-    uint64_t key = order_key(v, g.m);
+    uint64_t key = order_key(v, g.m * g.sym_bits);
     if (i == 0 || key < best) {
       best = key;
       mu = v;
@@ -116,8 +120,8 @@ __global__ void generic_query_kernel(Geom g, const uint8_t* __restrict__ seq, ui
       ++n_valid;
       n_pos += present ? 1 : 0;
       bool head = true;
-      if (p > 0) {
-        KmerView u = load_kmer(g, seq, seq_len, off, n_reads, p - 1);
+      if (p >= (uint64_t)g.sym_bytes) {
+        KmerView u = load_kmer(g, seq, seq_len, off, n_reads, p - (uint64_t)g.sym_bytes);
         if (u.valid && u.read == v.read && minimizer(g, u.fwd, u.rc) == mu) head = false;
       }
       n_runs += head ? 1 : 0;

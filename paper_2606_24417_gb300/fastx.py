@@ -91,8 +91,11 @@ class FastxReader:
     stays valid until the iterator is asked for the next one."""
 
     def __init__(self, src, k: int, batch_bytes: int = 64 << 20, max_pieces: int = 1 << 20,
-                 chunk_bytes: int = 16 << 20, pinned: bool | None = None):
+                 chunk_bytes: int = 16 << 20, pinned: bool | None = None, symbol_bytes: int = 1):
         self._lib = load_library()
+        if symbol_bytes != 1:
+            raise ValueError("FASTX batches split records at any byte; multi-byte symbols "
+                             "(DNA triplets) need whole records: use the host entry points")
         if pinned is None:
             try:
                 import torch
@@ -203,7 +206,7 @@ class FastxReader:
 
 def insert_fastx(filt, src, **reader_kw) -> dict:
     """Insert every record of a FASTA/FASTQ source (Alg. 1 over each record)."""
-    rd = FastxReader(src, filt.k, **reader_kw)
+    rd = FastxReader(src, filt.k, symbol_bytes=3 if filt.alphabet == 2 else 1, **reader_kw)
     t0 = time.perf_counter()
     bases = batches = 0
     for seq, off, _ in rd:
@@ -219,7 +222,7 @@ def query_fastx(filt, src, **reader_kw):
     """Per-record positive k-mer counts and k-mer positions of a FASTA/FASTQ
     source (Alg. 2 over each record): (hits uint64[records], kmers
     uint64[records], info dict)."""
-    rd = FastxReader(src, filt.k, **reader_kw)
+    rd = FastxReader(src, filt.k, symbol_bytes=3 if filt.alphabet == 2 else 1, **reader_kw)
     hits_rec = np.zeros(1024, dtype=np.uint64)
     kmers_rec = np.zeros(1024, dtype=np.uint64)
     hits_buf = _host_buffer(rd.max_pieces, np.uint32, rd.pinned)

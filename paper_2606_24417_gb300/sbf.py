@@ -49,7 +49,9 @@ def load_library() -> ctypes.CDLL:
             "sbf_create": (I, [I, I, I, I, U64, ctypes.POINTER(P)]),
             "sbf_create_ex": (I, [I, I, I, I, U64, I, I, ctypes.POINTER(P)]),
             "sbf_create_layout": (I, [I, I, I, I, U64, I, I, I, ctypes.POINTER(P)]),
+            "sbf_create_full": (I, [I, I, I, I, U64, I, I, I, I, ctypes.POINTER(P)]),
             "sbf_layout": (I, [P]),
+            "sbf_alphabet": (I, [P]),
             "sbf_destroy": (None, [P]),
             "sbf_info": (I, [P] + [ctypes.POINTER(I)] * 6 + [ctypes.POINTER(U64)]),
             "sbf_num_words": (U64, [P]),
@@ -136,15 +138,18 @@ class SuperBloomFilter:
     canonical: treat a k-mer and its reverse complement as one key;
     layout: LAYOUT_DEFAULT, or LAYOUT_PAPER for the paper's literal layout
     (256-bit shards, 2^P of them, shard = minimizer key & (2^P - 1), hash i
-    in 64-bit word i mod 4).
+    in 64-bit word i mod 4);
+    alphabet: "dna" (or 0), "protein" (1) or "dna_triplet" (2); the latter two
+    are forward only (pass canonical=False).
     """
 
     def __init__(self, k: int = 31, m: int = 16, s: int = 28, H: int = 4, bits: int = 1 << 30,
-                 shard_bits: int = 512, canonical: bool = True, layout: int = 0):
+                 shard_bits: int = 512, canonical: bool = True, layout: int = 0, alphabet=0):
         lib = load_library()
+        alphabet = ALPHABETS.get(alphabet, alphabet)
         h = ctypes.c_void_p()
-        _check(lib.sbf_create_layout(k, m, s, H, bits, shard_bits, 1 if canonical else 0, layout,
-                                     ctypes.byref(h)))
+        _check(lib.sbf_create_full(k, m, s, H, bits, shard_bits, 1 if canonical else 0, layout,
+                                   alphabet, ctypes.byref(h)))
         self._h = h
         self._lib = lib
         ki, mi, si, Hi, Bi, ci = (ctypes.c_int() for _ in range(6))
@@ -156,6 +161,7 @@ class SuperBloomFilter:
         self.n_shards = int(n.value)
         self.n_words = int(lib.sbf_num_words(h))
         self.layout = int(lib.sbf_layout(h))
+        self.alphabet = int(lib.sbf_alphabet(h))
 
     def close(self) -> None:
         h = getattr(self, "_h", None)
@@ -244,13 +250,15 @@ class SuperBloomFilter:
         _check(self._lib.sbf_set_bits(self._h, _host_ptr(w)))
 
     _MAGIC = b"SBFGB300"
-    _VERSION = 2  # version 1 had no layout field (layout 0)
+    _VERSION = 3  # version 1: no layout (0); version 2: no alphabet (DNA)
 
     def save(self, path: str) -> None:
         """Checkpoint: header (magic, version, k, m, s, H, shard_bits,
-        canonical, n_shards, layout) followed by the raw little-endian words."""
-        hdr = struct.pack("<8sIiiiiiiQi", self._MAGIC, self._VERSION, self.k, self.m, self.s,
-                          self.H, self.shard_bits, int(self.canonical), self.n_shards, self.layout)
+        canonical, n_shards, layout, alphabet) followed by the raw
+        little-endian words."""
+        hdr = struct.pack("<8sIiiiiiiQii", self._MAGIC, self._VERSION, self.k, self.m, self.s,
+                          self.H, self.shard_bits, int(self.canonical), self.n_shards, self.layout,
+                          self.alphabet)
         with open(path, "wb") as fh:
             fh.write(hdr)
             fh.write(self.words().astype("<u8").tobytes())
@@ -261,10 +269,12 @@ class SuperBloomFilter:
         with open(path, "rb") as fh:
             hdr = fh.read(size1)
             magic, ver, k, m, s, H, B, canon, n = struct.unpack("<8sIiiiiiiQ", hdr)
-            if magic != cls._MAGIC or ver not in (1, 2):
+            if magic != cls._MAGIC or ver not in (1, 2, 3):
                 raise SbfError(-1, f"{path}: not a filter checkpoint")
-            layout = struct.unpack("<i", fh.read(4))[0] if ver == 2 else 0
-            f = cls(k, m, s, H, n * B, shard_bits=B, canonical=bool(canon), layout=layout)
+            layout = struct.unpack("<i", fh.read(4))[0] if ver >= 2 else 0
+            alphabet = struct.unpack("<i", fh.read(4))[0] if ver >= 3 else 0
+            f = cls(k, m, s, H, n * B, shard_bits=B, canonical=bool(canon), layout=layout,
+                    alphabet=alphabet)
             w = np.frombuffer(fh.read(), dtype="<u8")
             f.set_words(w)
         return f
@@ -272,6 +282,8 @@ class SuperBloomFilter:
 
 BATCH_PER_FILTER, BATCH_FUSED, BATCH_GRAPH = 0, 1, 2
 LAYOUT_DEFAULT, LAYOUT_PAPER = 0, 1
+ALPHABET_DNA, ALPHABET_PROTEIN, ALPHABET_DNA_TRIPLET = 0, 1, 2
+ALPHABETS = {"dna": 0, "protein": 1, "dna_triplet": 2}
 
 
 class FilterBatch:

@@ -475,3 +475,50 @@ def batched_workload(n_filters: int = 256, exp_lo: int = 20, exp_hi: int = 28,
     np.cumsum(gl, out=goff[1:])
     return dict(bits=bits, genomes=genomes, gseq=gseq, goff=goff,
                 ggroup=np.arange(n_filters + 1, dtype=np.uint64), seq=seq, off=off, group=group)
+
+
+# ----------------------------------------------------------------------------
+# proteins (Sec. IV-A's 26-symbol alphabet; the 20 standard residues occur)
+# ----------------------------------------------------------------------------
+AMINO = np.frombuffer(b"ACDEFGHIKLMNPQRSTVWY", dtype=np.uint8)
+# residue frequencies in percent, rounded (typical of large protein databases)
+_AMINO_PCT = np.array([8.3, 1.4, 5.5, 6.8, 3.9, 7.1, 2.3, 5.9, 5.8, 9.7,
+                       2.4, 4.1, 4.7, 3.9, 5.5, 6.6, 5.4, 6.9, 1.1, 2.9])
+_AMINO_CDF = np.cumsum(_AMINO_PCT / _AMINO_PCT.sum())
+
+
+def protein_sequence(n: int, seed: int, dup_frac: float = 0.05) -> np.ndarray:
+    """n residues drawn i.i.d. from the frequencies above, then dup_frac of
+    them overwritten by copies of 50-300-residue segments (paralogous
+    domains), each copy with 10% substitutions."""
+    u = uniform01(seed, 11, 0, n)
+    out = AMINO[np.minimum(np.searchsorted(_AMINO_CDF, u, side="right"), 19)]
+    if dup_frac > 0 and n > 1000:
+        budget = int(dup_frac * n)
+        lens = randint(seed, 12, max(1, budget // 50), 50, 301)
+        lens = lens[: max(1, int(np.searchsorted(np.cumsum(lens), budget)))]
+        src = randint(seed, 13, lens.size, 0, n - 301)
+        dst = randint(seed, 14, lens.size, 0, n - 301)
+        for i, L in enumerate(lens):
+            seg = out[src[i]:src[i] + L].copy()
+            mut = uniform01(seed, 15, int(i) * 301, int(L)) < 0.10
+            seg[mut] = AMINO[randint(seed, 16, int(mut.sum()), 0, 20, start=int(i) * 301)]
+            out[dst[i]:dst[i] + L] = seg
+    return out
+
+
+def sample_peptides(proteome: np.ndarray, n: int, length: int, error_rate: float,
+                    seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """n peptides of `length` residues from uniform positions, each residue
+    substituted (uniformly among the 20) with probability error_rate."""
+    starts = randint(seed, 21, n, 0, proteome.size - length + 1)
+    idx = starts[:, None] + np.arange(length)[None, :]
+    seq = proteome[idx].reshape(-1).copy()
+    mut = uniform01(seed, 22, 0, seq.size) < error_rate
+    seq[mut] = AMINO[randint(seed, 23, int(mut.sum()), 0, 20)]
+    return seq, fixed_length_offsets(n, length)
+
+
+def random_peptides(n: int, length: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """n peptides of i.i.d. residues (the same frequencies)."""
+    return protein_sequence(n * length, seed, dup_frac=0.0), fixed_length_offsets(n, length)
