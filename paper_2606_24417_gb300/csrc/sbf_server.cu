@@ -93,6 +93,20 @@ struct Launch {
   int slot = 0;
 };
 
+// Zeroes each segment's hit counts and answer words (when it has them) before
+// the query: one launch for a whole batch of requests instead of two memsets
+// per request.  Block b handles segments b, b + gridDim.x, ...
+__global__ void zero_segments(const Segment* __restrict__ segs, uint32_t n_segs) {
+  for (uint32_t i = blockIdx.x; i < n_segs; i += gridDim.x) {
+    const Segment sg = segs[i];
+    for (uint64_t j = threadIdx.x; j < sg.n_reads; j += blockDim.x) sg.hits[j] = 0u;
+    if (sg.bits) {
+      const uint64_t nw = (sg.seq_len + 31) / 32;
+      for (uint64_t j = threadIdx.x; j < nw; j += blockDim.x) sg.bits[j] = 0u;
+    }
+  }
+}
+
 }  // namespace
 
 struct sbf_server {
@@ -117,6 +131,8 @@ struct sbf_server {
   std::unordered_map<uint64_t, Request*> by_id;
   std::vector<Launch> inflight;
   uint64_t next_id = 1;
+  uint64_t completions = 0;     // launches whose stream work has finished (host callbacks)
+  uint64_t submissions = 0;     // requests submitted so far
   bool stop = false;
   std::thread worker;
   // statistics
@@ -130,6 +146,17 @@ namespace {
 
 using sbf::cuda_fail;
 using sbf::fail;
+
+// Runs on a CUDA callback thread once a launch's stream work is done: counts
+// the completion and wakes the worker (no CUDA calls allowed here).
+void CUDART_CB on_launch_done(void* arg) {
+  sbf_server* s = static_cast<sbf_server*>(arg);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    ++s->completions;
+  }
+  s->cv_work.notify_all();
+}
 
 // Launch every request of `L` as one segment each, on slot L.slot.
 int start_launch(sbf_server* s, Launch& L) {
@@ -145,9 +172,7 @@ int start_launch(sbf_server* s, Launch& L) {
     uint64_t* d_off = reinterpret_cast<uint64_t*>(s->d_meta + r->meta_at);
     uint32_t* d_hits = reinterpret_cast<uint32_t*>(d_off + r->n_reads + 1);
     if ((e = cudaMemcpyAsync(s->d_seq + r->seq_at, r->h_seq, r->seq_len, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(d_off, r->h_off, (r->n_reads + 1) * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(d_hits, 0, r->n_reads * 4, st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(s->d_bits + r->seq_at / 32, 0, r->seq_bytes / 8, st)) != cudaSuccess)
+        (e = cudaMemcpyAsync(d_off, r->h_off, (r->n_reads + 1) * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return cuda_fail(e, "server staging");
     Segment sg{};
     sg.words = g.words;
@@ -156,7 +181,7 @@ int start_launch(sbf_server* s, Launch& L) {
     sg.seq_len = r->seq_len;
     sg.off = d_off;
     sg.n_reads = r->n_reads;
-    sg.bits = s->d_bits + r->seq_at / 32;
+    sg.bits = r->h_bits ? s->d_bits + r->seq_at / 32 : nullptr;  // no answer words wanted: none written
     sg.hits = d_hits;
     sg.p_begin = 0;
     sg.iter_begin = iters;
@@ -167,6 +192,11 @@ int start_launch(sbf_server* s, Launch& L) {
   if ((e = cudaMemcpyAsync(s->d_tables[slot], table, L.reqs.size() * sizeof(Segment),
                            cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return cuda_fail(e, "server table upload");
+  {
+    const uint32_t n = (uint32_t)L.reqs.size();
+    zero_segments<<<n < 1024u ? n : 1024u, 256, 0, st>>>(s->d_tables[slot], n);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "server zeroing");
+  }
   Params P{};
   P.g = g;
   P.stats = nullptr;
@@ -189,6 +219,9 @@ int start_launch(sbf_server* s, Launch& L) {
       return cuda_fail(e, "server results");
   }
   if ((e = cudaEventRecord(s->events[slot], st)) != cudaSuccess) return cuda_fail(e, "server event");
+  // wake the worker when this launch's work is done instead of letting it poll
+  if ((e = cudaLaunchHostFunc(st, on_launch_done, s)) != cudaSuccess)
+    return cuda_fail(e, "server completion callback");
   return SBF_OK;
 }
 
@@ -264,11 +297,12 @@ void worker_loop(sbf_server* s) {
       }
       continue;
     }
-    // nothing to admit: wait for a submission or poll in-flight work
-    if (s->inflight.empty())
-      s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
-    else
-      s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+    // nothing to admit: wait for a submission or a completion callback (the
+    // timeout only bounds the wait; callbacks and submissions notify)
+    const uint64_t seen_c = s->completions, seen_s = s->submissions;
+    s->cv_work.wait_for(lk, std::chrono::milliseconds(s->inflight.empty() ? 5 : 1), [&] {
+      return s->completions != seen_c || s->submissions != seen_s || s->stop;
+    });
   }
 }
 
@@ -394,6 +428,7 @@ int sbf_server_submit(sbf_server* s, const uint8_t* h_seq, uint64_t seq_len, con
     }
     s->by_id[r->id] = r;
     s->queue.push_back(r);
+    ++s->submissions;
     *ticket = r->id;
   }
   s->cv_work.notify_one();
