@@ -309,7 +309,7 @@ def bacterial():
     return g, q, qoff
 
 
-def test_bacterial_full_size_sampled(bacterial):
+def test_bacterial_full_size(bacterial, tmp_path):
     g, q, qoff = bacterial
     params = (31, 16, 28, 4, 1 << 30, 512, True)
     f = make_filter(*params[:5], params[5], params[6])
@@ -341,3 +341,21 @@ def test_bacterial_full_size_sampled(bacterial):
     # sampled reads from the genome are mostly positive, random reads almost never
     n = (qoff.size - 1) // 2
     assert hits[:n].mean() > 20 and hits[n:].mean() < 0.05
+    # every read: the oracle, holding the (identical) filter words, answers all
+    # 20M reads in parallel processes; chunks of 262,144 reads start at
+    # multiples of 32 bytes (150 * 262144 = 32 * 1228800), so answer words
+    # compare word for word (the last word of a chunk up to its end)
+    from oracle_pool import query_all
+
+    words = o.words()
+    checked = 0
+    for r0, r1, a, b, obits, ohits in query_all(params, words, q, qoff, str(tmp_path)):
+        assert a % 32 == 0
+        assert np.array_equal(hits[r0:r1], ohits), (r0, r1)
+        w0, nw = a // 32, (b - a + 31) // 32
+        gw = bits[w0:w0 + nw].copy()
+        if (b - a) % 32:
+            gw[-1] &= np.uint32((1 << ((b - a) % 32)) - 1)
+        assert np.array_equal(gw, obits), (r0, r1)
+        checked += r1 - r0
+    assert checked == qoff.size - 1
