@@ -252,8 +252,11 @@ int sbf_batch_query_noalloc(sbf_filter* const* filters, int n_filters, const uin
  * Not in the paper.
  *
  * sbf_server_create: the filter (with a fused kernel) stays resident; the
- *   server owns read_budget_bytes of device memory for request reads (plus a
- *   quarter of that for offsets and hit counts) and a worker thread.  Queued
+ *   server owns read_budget_bytes of device memory for request reads (plus
+ *   three eighths of that for offsets, hit counts and answer words), pinned
+ *   host memory of three eighths of it where results land before they are
+ *   copied to the caller's buffers (so result buffers may be pageable), and
+ *   a worker thread.  Queued
  *   requests are admitted while that memory has room, every request admitted
  *   at one moment (at most max_per_launch of them, 1..65536) is served by ONE
  *   kernel launch (one segment each), and up to max_inflight (1..16)

@@ -118,6 +118,11 @@ struct sbf_server {
   uint8_t* d_seq = nullptr;     // reads
   uint32_t* d_bits = nullptr;   // answers, one bit per read-arena byte
   uint8_t* d_meta = nullptr;    // offsets and hit counts
+  // pinned host mirrors of the result arenas: results land here
+  // asynchronously and are copied to the caller's buffers after completion
+  // (a device-to-host copy into pageable memory would block the worker)
+  uint8_t* h_meta = nullptr;
+  uint32_t* h_bits = nullptr;
   std::unique_ptr<Arena> seq_arena, meta_arena;
   // per launch slot: stream, event, segment tables
   std::vector<cudaStream_t> streams;
@@ -208,14 +213,14 @@ int start_launch(sbf_server* s, Launch& L) {
   P.grid_blocks = 0;
   if ((e = sbf::fused::launch_params(P, false, st)) != cudaSuccess) return cuda_fail(e, "server launch");
   for (Request* r : L.reqs) {
-    const uint64_t* d_off = reinterpret_cast<const uint64_t*>(s->d_meta + r->meta_at);
-    const uint32_t* d_hits = reinterpret_cast<const uint32_t*>(d_off + r->n_reads + 1);
+    const uint64_t hits_at = r->meta_at + (r->n_reads + 1) * 8;
     if (r->h_hits && r->n_reads &&
-        (e = cudaMemcpyAsync(r->h_hits, d_hits, r->n_reads * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        (e = cudaMemcpyAsync(s->h_meta + hits_at, s->d_meta + hits_at, r->n_reads * 4,
+                             cudaMemcpyDeviceToHost, st)) != cudaSuccess)
       return cuda_fail(e, "server results");
     if (r->h_bits && r->seq_len &&
-        (e = cudaMemcpyAsync(r->h_bits, s->d_bits + r->seq_at / 32, ((r->seq_len + 31) / 32) * 4,
-                             cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        (e = cudaMemcpyAsync(s->h_bits + r->seq_at / 32, s->d_bits + r->seq_at / 32,
+                             ((r->seq_len + 31) / 32) * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
       return cuda_fail(e, "server results");
   }
   if ((e = cudaEventRecord(s->events[slot], st)) != cudaSuccess) return cuda_fail(e, "server event");
@@ -223,6 +228,17 @@ int start_launch(sbf_server* s, Launch& L) {
   if ((e = cudaLaunchHostFunc(st, on_launch_done, s)) != cudaSuccess)
     return cuda_fail(e, "server completion callback");
   return SBF_OK;
+}
+
+// Copy a finished launch's results from the pinned mirrors to the callers'
+// buffers (no lock needed: the requests' arena space is still theirs).
+void deliver(sbf_server* s, const Launch& L) {
+  for (const Request* r : L.reqs) {
+    if (r->h_hits && r->n_reads)
+      std::memcpy(r->h_hits, s->h_meta + r->meta_at + (r->n_reads + 1) * 8, r->n_reads * 4);
+    if (r->h_bits && r->seq_len)
+      std::memcpy(r->h_bits, s->h_bits + r->seq_at / 32, ((r->seq_len + 31) / 32) * 4);
+  }
 }
 
 void finish(sbf_server* s, Launch& L, int status) {
@@ -246,15 +262,23 @@ void worker_loop(sbf_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
-    // retire finished launches
+    // retire finished launches: results are copied out without the lock
+    std::vector<std::pair<Launch, int>> done;
     for (size_t i = 0; i < s->inflight.size();) {
       cudaError_t q = cudaEventQuery(s->events[s->inflight[i].slot]);
       if (q == cudaErrorNotReady) {
         ++i;
         continue;
       }
-      finish(s, s->inflight[i], q == cudaSuccess ? SBF_OK : SBF_ECUDA);
+      done.emplace_back(std::move(s->inflight[i]), q == cudaSuccess ? SBF_OK : SBF_ECUDA);
       s->inflight.erase(s->inflight.begin() + i);
+    }
+    if (!done.empty()) {
+      lk.unlock();
+      for (auto& d : done)
+        if (d.second == SBF_OK) deliver(s, d.first);
+      lk.lock();
+      for (auto& d : done) finish(s, d.first, d.second);
       s->cv_done.notify_all();
     }
     if (s->stop && s->queue.empty() && s->inflight.empty()) break;
@@ -331,7 +355,9 @@ int sbf_server_create(const sbf_filter* f, uint64_t read_budget_bytes, int max_i
   cudaSetDevice(s->device);
   bool ok = cudaMalloc(&s->d_seq, seq_bytes) == cudaSuccess &&
             cudaMalloc(&s->d_bits, seq_bytes / 8) == cudaSuccess &&
-            cudaMalloc(&s->d_meta, meta_bytes) == cudaSuccess;
+            cudaMalloc(&s->d_meta, meta_bytes) == cudaSuccess &&
+            cudaMallocHost(&s->h_bits, seq_bytes / 8) == cudaSuccess &&
+            cudaMallocHost(&s->h_meta, meta_bytes) == cudaSuccess;
   s->streams.resize(max_inflight);
   s->events.resize(max_inflight);
   s->h_tables.resize(max_inflight);
@@ -385,6 +411,8 @@ void sbf_server_destroy(sbf_server* s) {
   cudaFree(s->d_seq);
   cudaFree(s->d_bits);
   cudaFree(s->d_meta);
+  cudaFreeHost(s->h_bits);
+  cudaFreeHost(s->h_meta);
   cudaSetDevice(prev);
   for (auto& kv : s->by_id) delete kv.second;
   delete s;
