@@ -192,6 +192,10 @@ void sbf_destroy(sbf_filter* f) {
   }
   cudaFree(f->geom.words);
   cudaFreeHost(f->host_first);
+  for (int i = 0; i < 2; ++i) {
+    cudaFreeHost(f->host_stage_bits[i]);
+    cudaFreeHost(f->host_stage_hits[i]);
+  }
   delete f;
 }
 
@@ -388,6 +392,46 @@ int ensure_host_buffers(sbf_filter* f, uint64_t seq_cap, uint64_t reads_cap) {
   return SBF_OK;
 }
 
+// True if p is host memory the device can copy to without staging (pinned
+// or registered); false for pageable memory (and NULL).
+bool is_pinned(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+int ensure_stage(sbf_filter* f, uint64_t words, uint64_t reads) {
+  if (words > f->host_stage_words) {
+    for (int i = 0; i < 2; ++i) {
+      cudaFreeHost(f->host_stage_bits[i]);
+      f->host_stage_bits[i] = nullptr;
+      if (cudaMallocHost(&f->host_stage_bits[i], words * 4) != cudaSuccess) {
+        cudaGetLastError();
+        f->host_stage_words = 0;
+        return fail(SBF_ENOMEM, "pinned staging allocation failed");
+      }
+    }
+    f->host_stage_words = words;
+  }
+  if (reads > f->host_stage_reads) {
+    for (int i = 0; i < 2; ++i) {
+      cudaFreeHost(f->host_stage_hits[i]);
+      f->host_stage_hits[i] = nullptr;
+      if (cudaMallocHost(&f->host_stage_hits[i], reads * 4) != cudaSuccess) {
+        cudaGetLastError();
+        f->host_stage_reads = 0;
+        return fail(SBF_ENOMEM, "pinned staging allocation failed");
+      }
+    }
+    f->host_stage_reads = reads;
+  }
+  return SBF_OK;
+}
+
 // Host path of filters with fused kernels.  A chunk's bytes are copied from
 // the 32-aligned position A <= off[r0], and the kernel takes the caller's
 // offsets unchanged: its sequence and answer pointers are shifted back by A
@@ -408,12 +452,30 @@ int host_run_fused(sbf_filter* f, bool is_query, const uint8_t* h_seq, const uin
   const uint64_t adv = (uint64_t)fused::advance_of(f->geom);
   uint32_t* first_words = ensure_first_words(f, chunks.size());
   if (!first_words) return fail(SBF_ENOMEM, "pinned host allocation failed");
+  // pageable output buffers: answers go through pinned staging, copied out
+  // when their buffer set is next needed (or at the end)
+  const bool stage_bits = is_query && h_bits && !is_pinned(h_bits);
+  const bool stage_hits = is_query && h_hits && !is_pinned(h_hits);
+  if ((stage_bits || stage_hits) &&
+      (rc = ensure_stage(f, stage_bits ? (seq_cap + 31) / 32 + 1 : 0, stage_hits ? reads_cap : 0)) != SBF_OK)
+    return rc;
+  int64_t pending[2] = {-1, -1};  // chunk whose staged answers buffer set b still holds
+  auto copy_out = [&](int b) {
+    if (pending[b] < 0) return;
+    const Chunk& c = chunks[(size_t)pending[b]];
+    const uint64_t nr = c.r1 - c.r0, nwords = (c.end - c.a + 31) / 32;
+    if (stage_hits) std::memcpy(h_hits + c.r0, f->host_stage_hits[b], nr * 4);
+    if (stage_bits && nwords > 1)
+      std::memcpy(h_bits + c.a / 32 + 1, f->host_stage_bits[b] + 1, (nwords - 1) * 4);
+    pending[b] = -1;
+  };
   for (size_t ci = 0; ci < chunks.size(); ++ci) {
     const Chunk& c = chunks[ci];
     const int b = (int)(ci & 1);
     cudaStream_t st = f->host_streams[b];
     cudaError_t e = cudaStreamSynchronize(st);  // buffer set b is free again
     if (e != cudaSuccess) return cuda_fail(e, "host path sync");
+    copy_out(b);
     const uint64_t len = c.end - c.a, nr = c.r1 - c.r0, nwords = (len + 31) / 32;
     if ((e = cudaMemcpyAsync(f->host_dev_seq[b], h_seq + c.a, len, cudaMemcpyHostToDevice, st)) !=
             cudaSuccess ||
@@ -450,12 +512,15 @@ int host_run_fused(sbf_filter* f, bool is_query, const uint8_t* h_seq, const uin
     P.chunk = 1;
     P.grid_blocks = 0;
     if ((e = fused::launch_params(P, !is_query, st)) != cudaSuccess) return cuda_fail(e, "host path launch");
+    uint32_t* hits_dst = stage_hits ? f->host_stage_hits[b] : h_hits + c.r0;
+    uint32_t* bits_dst = stage_bits ? f->host_stage_bits[b] + 1 : h_bits + c.a / 32 + 1;
+    if (stage_bits || stage_hits) pending[b] = (int64_t)ci;
     if (want_hits &&
-        (e = cudaMemcpyAsync(h_hits + c.r0, f->host_dev_hits[b], nr * 4, cudaMemcpyDeviceToHost, st)) !=
+        (e = cudaMemcpyAsync(hits_dst, f->host_dev_hits[b], nr * 4, cudaMemcpyDeviceToHost, st)) !=
             cudaSuccess)
       return cuda_fail(e, "host path D2H");
     if (want_bits) {
-      if (nwords > 1 && (e = cudaMemcpyAsync(h_bits + c.a / 32 + 1, f->host_dev_bits[b] + 1,
+      if (nwords > 1 && (e = cudaMemcpyAsync(bits_dst, f->host_dev_bits[b] + 1,
                                              (nwords - 1) * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(e, "host path D2H");
       if ((e = cudaMemcpyAsync(&first_words[ci], f->host_dev_bits[b], 4, cudaMemcpyDeviceToHost, st)) !=
@@ -466,6 +531,7 @@ int host_run_fused(sbf_filter* f, bool is_query, const uint8_t* h_seq, const uin
   for (int b = 0; b < 2; ++b) {
     cudaError_t e = cudaStreamSynchronize(f->host_streams[b]);
     if (e != cudaSuccess) return cuda_fail(e, "host path sync");
+    copy_out(b);
   }
   if (is_query && h_bits) {
     // word A/32 of a chunk: its bits below off[r0] belong to the previous chunk

@@ -27,6 +27,12 @@ struct sbf_filter {
   // destination would make the copy synchronous and stall the pipeline)
   uint32_t* host_first = nullptr;
   uint64_t host_first_cap = 0;
+  // pinned staging of a chunk's answers when the caller's output buffers are
+  // pageable (a copy into pageable memory would wait for the chunk's kernel
+  // and stop the next chunk's upload from overlapping it)
+  uint32_t* host_stage_bits[2] = {nullptr, nullptr};
+  uint32_t* host_stage_hits[2] = {nullptr, nullptr};
+  uint64_t host_stage_words = 0, host_stage_reads = 0;
 };
 
 namespace sbf {

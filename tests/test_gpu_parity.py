@@ -216,6 +216,12 @@ def test_host_path_matches_device(monkeypatch, params):
     hb, hh = f.query_host(q_seq, q_off)
     ob, oh = o.query(q_seq, q_off)
     assert np.array_equal(hb, ob) and np.array_equal(hh, oh)
+    # pinned output buffers (answers copied straight in) give the same as the
+    # pageable ones above (answers staged through pinned memory)
+    pb = torch.empty(hb.size, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+    ph = torch.empty(hh.size, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+    f.query_host(q_seq, q_off, bits=pb, hits=ph)
+    assert np.array_equal(pb, ob) and np.array_equal(ph, oh)
     monkeypatch.delenv("SBF_HOST_CHUNK_BYTES")
     hb2, hh2 = f.query_host(q_seq, q_off)
     assert np.array_equal(hb2, ob) and np.array_equal(hh2, oh)
