@@ -655,18 +655,34 @@ def run_served(args):
     log(f"[bench] {n_pool} requests, {sum(p[0].size for p in pool) / 1e6:.0f} Mbp, "
         f"mean {mean_kmers / 1e3:.0f}k k-mers")
 
-    def backlog(srv, reps=2):
+    def backlog(srv, reps=2, clients=1):
+        """Every pool request `reps` times, submitted by `clients` threads at
+        once (ctypes releases the GIL during each submit), then waited for."""
         srv.reset_stats()
-        tickets = [srv.submit(p[0], p[1]) for _ in range(reps) for p in pool]
+        work = [p for _ in range(reps) for p in pool]
+        tickets = [None] * len(work)
+
+        def client(c):
+            for i in range(c, len(work), clients):
+                tickets[i] = srv.submit(work[i][0], work[i][1])
+
+        ths = [threading.Thread(target=client, args=(c,)) for c in range(clients)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
         for tk in tickets:
             srv.wait(tk, 600)
-        return srv.stats()
+        st = srv.stats()
+        st["clients"] = clients
+        return st
 
     out = {}
     srv = FilterServer(f, read_budget_bytes=1 << 30, max_inflight=3)
     backlog(srv, 1)  # warm
     peak = backlog(srv)
     out["peak"] = peak
+    out["peak_4_clients"] = backlog(srv, clients=4)
     one = FilterServer(f, read_budget_bytes=1 << 30, max_inflight=3, max_per_launch=1)
     backlog(one, 1)
     out["one_launch_per_request"] = backlog(one)
@@ -975,6 +991,20 @@ def run_fastx(args):
             res[name] = {"kmers_per_s": q_kmers / t_q, "seconds": t_q,
                          "text_bytes": qi["text_bytes"], "parse_seconds": qi["parse_seconds"],
                          "batches": qi["batches"], "positives": int(hits.sum())}
+        # the same files tokenised on the device (raw text over the link)
+        from paper_2606_24417_gb300.fastx import DeviceFastx
+
+        dfx = DeviceFastx(f)
+        t_dins, dinfo = best(lambda: (f.clear(), dfx.insert(fa))[1])
+        same_dev = bool(np.array_equal(f.words(), want))
+        res["fasta_insert_device_parse"] = {"kmers_per_s": ins_kmers / t_dins, "seconds": t_dins,
+                                            "text_bytes": os.path.getsize(fa),
+                                            "host_fallback_chunks": dinfo["host_fallback_chunks"]}
+        for name, path in (("fastq_query_device_parse", fq), ("fastq_gz_query_device_parse", fqz)):
+            t_q, (hits, kmers, qi) = best(lambda: dfx.query(path))
+            res[name] = {"kmers_per_s": q_kmers / t_q, "seconds": t_q,
+                         "positives": int(hits.sum()),
+                         "host_fallback_chunks": qi["host_fallback_chunks"]}
         # the same work from host arrays and from device-resident inputs
         h_genome = torch.from_numpy(genome).pin_memory().numpy()
         h_goff = np.array([0, genome.size], dtype=np.uint64)
@@ -991,7 +1021,9 @@ def run_fastx(args):
         t_di, _ = best(lambda: (f.clear(), f.insert(dg, dgo)))
         t_dq, _ = best(lambda: f.query(dq, dqo, hits=hits_d, want_bits=False))
         agree = int(hh.astype(np.int64).sum()) == res["fastq_query"]["positives"] == \
-            res["fastq_gz_query"]["positives"] == int(hits_d.sum().item())
+            res["fastq_gz_query"]["positives"] == int(hits_d.sum().item()) == \
+            res["fastq_query_device_parse"]["positives"] == \
+            res["fastq_gz_query_device_parse"]["positives"] and same_dev
         res["host_arrays"] = {"insert_kmers_per_s": ins_kmers / t_hi,
                               "query_kmers_per_s": q_kmers / t_hq}
         res["device_resident"] = {"insert_kmers_per_s": ins_kmers / t_di,

@@ -327,6 +327,25 @@ int sbf_fastx_parse(sbf_fastx* p, const uint8_t* text, uint64_t text_len, int fi
                     uint64_t pieces_cap, uint64_t* n_pieces, uint64_t* seq_len,
                     uint64_t* consumed);
 
+/* FASTA / FASTQ on the device.  sbf_fastx_parse_device turns a chunk of
+ * whole records in device memory (d_text, 16-byte aligned, text_len bytes,
+ * starting at a record's header line and ending with '\n') into a read batch
+ * in device memory: d_seq receives the records' sequence bytes back to back
+ * (at most text_len bytes), d_off the n + 1 record offsets (max_records + 1
+ * entries).  fastq = 0: FASTA (records start at lines beginning with '>';
+ * sequence lines lose '\r', ' ' and '\t'); fastq = 1: four-line FASTQ
+ * records.  The bytes kept are exactly those sbf_fastx_parse keeps.  On
+ * return (the call synchronises `stream`) h_result[0] = records, [1] =
+ * sequence bytes, [2] = 1 if the chunk is outside these shapes (a FASTA line
+ * starting with '@', a FASTQ record not of four lines, a quality line of
+ * another length): then nothing usable was written and the chunk should go
+ * through sbf_fastx_parse.  d_scratch (16-byte aligned) needs
+ * sbf_fastx_device_scratch(text_len) bytes (about 9 per text byte). */
+int sbf_fastx_device_scratch(uint64_t text_len, uint64_t* scratch_bytes);
+int sbf_fastx_parse_device(const uint8_t* d_text, uint64_t text_len, int fastq, uint8_t* d_seq,
+                           uint64_t* d_off, uint64_t max_records, void* d_scratch,
+                           uint64_t scratch_bytes, uint64_t* h_result, sbf_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Random-sector bandwidth probe.  Measurement only; not a step of the method.
  *

@@ -245,3 +245,245 @@ def query_fastx(filt, src, **reader_kw):
     return hits_rec[:n_rec], kmers_rec[:n_rec], {
         "records": n_rec, "batches": batches, "text_bytes": rd.text_bytes,
         "seconds": time.perf_counter() - t0, "parse_seconds": rd.parse_seconds}
+
+
+# ---------------------------------------------------------------------------
+# parsing on the device: the host moves raw text, the GPU tokenises it
+# ---------------------------------------------------------------------------
+def _fastq_start_ok(win: bytes, q: int) -> bool:
+    """True if a FASTQ record starts at win[q] and its four lines lie in win."""
+    parts = win[q:].split(b"\n", 4)
+    if len(parts) < 5:
+        return False
+    h, sq, plus, qual = parts[:4]
+    return (h[:1] == b"@" and plus[:1] == b"+"
+            and len(sq.rstrip(b"\r")) == len(qual.rstrip(b"\r")))
+
+
+def _last_record_start(buf: np.ndarray, lo: int, hi: int, fastq: bool) -> int:
+    """Position in (lo, hi) of the last record start of buf[lo:hi], or -1."""
+    win_len = 1 << 20
+    while True:
+        a = max(lo, hi - win_len)
+        win = buf[a:hi].tobytes()
+        if fastq:
+            j = len(win)
+            while True:
+                j = win.rfind(b"\n@", 0, j)
+                if j < 0:
+                    break
+                if _fastq_start_ok(win, j + 1):
+                    if a + j + 1 > lo:
+                        return a + j + 1
+                    break
+        else:
+            j = win.rfind(b"\n>")
+            if j >= 0 and a + j + 1 > lo:
+                return a + j + 1
+        if a == lo:
+            return -1
+        win_len *= 4
+
+
+def record_chunks(src, owner):
+    """Yields (buffer, start, end, fastq) with buffer[start:end] whole records
+    ending in '\\n'.  owner.bufs holds two buffers of owner.cap + 16 bytes used
+    in turn (a chunk stays valid until the next-but-one is produced); when a
+    record does not fit, owner.grow() is called and must double owner.cap
+    (with new buffers)."""
+    if isinstance(src, str):
+        with open(src, "rb") as fh:
+            gz = fh.read(2) == _GZIP_MAGIC
+    else:
+        gz = bytes(src[:2]) == _GZIP_MAGIC
+    fh = open(src, "rb") if isinstance(src, str) and not gz else None
+    pieces = None if fh is not None else text_chunks(src, 16 << 20)
+    pend = b""  # decompressed bytes not yet placed
+    carry = np.zeros(0, dtype=np.uint8)
+    first, fastq, i, eof = True, None, 0, False
+    try:
+        while not eof or carry.size:
+            buf = owner.bufs[i % 2]
+            i += 1
+            n = carry.size
+            buf[:n] = carry
+            s0 = 0
+            while True:
+                cap = owner.cap
+                while n < cap and not eof:  # fill the rest of the buffer
+                    if fh is not None:
+                        got = fh.readinto(memoryview(buf)[n:cap])
+                        if not got:
+                            eof = True
+                        n += got or 0
+                    else:
+                        if not pend:
+                            pend = next(pieces, b"")
+                            if not pend:
+                                eof = True
+                                break
+                        take = min(len(pend), cap - n)
+                        buf[n:n + take] = np.frombuffer(pend, dtype=np.uint8, count=take)
+                        pend = pend[take:]
+                        n += take
+                if first:  # skip anything before the first record
+                    head = buf[:min(n, 1 << 20)].tobytes()
+                    if head[:1] not in (b">", b"@"):
+                        cand = [j for j in (head.find(b"\n>"), head.find(b"\n@")) if j >= 0]
+                        if not cand:
+                            return
+                        s0 = min(cand) + 1
+                    fastq = bool(buf[s0] == ord("@"))
+                    first = False
+                if eof:
+                    break
+                cut = _last_record_start(buf, s0, n, fastq)
+                if cut > s0:
+                    break
+                old = buf[:n].copy()  # one record fills the buffer: grow and go on
+                owner.grow()
+                buf = owner.bufs[(i - 1) % 2]
+                buf[:n] = old
+            if eof:
+                end = n
+                if end > s0 and buf[end - 1] != ord("\n"):
+                    buf[end] = ord("\n")
+                    end += 1
+                carry = np.zeros(0, dtype=np.uint8)
+                if end > s0:
+                    yield buf, s0, end, fastq
+                return
+            carry = buf[cut:n].copy()
+            yield buf, s0, cut, fastq
+    finally:
+        if fh is not None:
+            fh.close()
+
+
+class DeviceFastx:
+    """Insert or query FASTA/FASTQ with the tokenising on the GPU: raw text is
+    copied to the device in chunks of whole records and parsed there
+    (sbf_fastx_parse_device) into a read batch that the filter's kernels take
+    directly.  Chunks the device parser does not accept (multi-line FASTQ,
+    mixed formats) go through the host parser.  Gzip input is decompressed on
+    the host first.  A chunk holds whole records; when one record does not
+    fit (512 MB by default, more than any human chromosome), the buffers are
+    doubled until it does."""
+
+    def __init__(self, filt, chunk_bytes: int = 512 << 20):
+        import torch
+
+        if filt.alphabet == 2:
+            raise ValueError("multi-byte symbols (DNA triplets) need the host entry points")
+        self.f, self.k, self.cap = filt, filt.k, chunk_bytes
+        self._lib = load_library()
+        self._torch = torch
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+        self._alloc(chunk_bytes)
+        self.stream = torch.cuda.Stream(device=self.dev)
+        self.h_off = torch.empty(0, dtype=torch.int64)   # pinned, grown on demand
+        self.h_hits = torch.empty(0, dtype=torch.int32)
+        self.result = (ctypes.c_uint64 * 3)()
+        self.stats = {"chunks": 0, "host_fallback_chunks": 0, "records": 0, "bases": 0,
+                      "text_bytes": 0, "seconds": 0.0}
+
+    def _alloc(self, cap: int) -> None:
+        torch = self._torch
+        self.cap = cap
+        self.bufs = [torch.empty(cap + 16, dtype=torch.uint8).pin_memory().numpy() for _ in range(2)]
+        self.max_records = cap // 2 + 2  # a record takes at least 2 bytes
+        self.d_text = torch.empty(cap + 16, dtype=torch.uint8, device=self.dev)
+        self.d_seq = torch.empty(cap + 16, dtype=torch.uint8, device=self.dev)
+        self.d_off = torch.empty(self.max_records + 1, dtype=torch.int64, device=self.dev)
+        need = ctypes.c_uint64()
+        _check(self._lib.sbf_fastx_device_scratch(cap + 16, ctypes.byref(need)))
+        self.scratch = torch.empty(int(need.value) + 16, dtype=torch.uint8, device=self.dev)
+        self.scratch_bytes = int(need.value)
+
+    def grow(self) -> None:
+        """Double the chunk size (a record did not fit)."""
+        self.stream.synchronize()
+        self.stats["grown_to"] = 2 * self.cap
+        self._alloc(2 * self.cap)
+
+    def _parse(self, buf, s0, end, fastq):
+        """Device batch (seq, off, n_records) of one chunk, or None if the
+        device parser rejected it."""
+        torch = self._torch
+        n = end - s0
+        with torch.cuda.stream(self.stream):
+            self.d_text[:n].copy_(torch.from_numpy(buf[s0:end]), non_blocking=True)
+        _check(self._lib.sbf_fastx_parse_device(
+            self.d_text.data_ptr(), n, 1 if fastq else 0, self.d_seq.data_ptr(), self.d_off.data_ptr(),
+            self.max_records, self.scratch.data_ptr(), self.scratch_bytes, self.result,
+            self.stream.cuda_stream))
+        n_rec, kept, bad = int(self.result[0]), int(self.result[1]), int(self.result[2])
+        self.stats["chunks"] += 1
+        self.stats["text_bytes"] += n
+        if bad:
+            return None
+        return self.d_seq[:kept], self.d_off[:n_rec + 1], n_rec
+
+    def _host_batches(self, buf, s0, end):
+        self.stats["host_fallback_chunks"] += 1
+        rd = FastxReader(bytes(buf[s0:end]), self.k, batch_bytes=max(1 << 20, end - s0 + 64),
+                         max_pieces=self.max_records, pinned=False)
+        for seq, off, rec in rd:
+            yield seq, off, rec, rd
+
+    def insert(self, src) -> dict:
+        t0 = time.perf_counter()
+        for buf, s0, end, fastq in record_chunks(src, self):
+            b = self._parse(buf, s0, end, fastq)
+            if b is None:
+                for seq, off, _, _ in self._host_batches(buf, s0, end):
+                    self.f.insert_host(seq, off)
+                    self.stats["bases"] += seq.size
+                continue
+            seq, off, n_rec = b
+            self.f.insert(seq, off, stream=self.stream)
+            self.stats["records"] += n_rec
+            self.stats["bases"] += seq.numel()
+        self.stream.synchronize()
+        self.stats["seconds"] = time.perf_counter() - t0
+        return dict(self.stats)
+
+    def query(self, src):
+        """Per-record positive k-mers and k-mer positions (as query_fastx)."""
+        torch = self._torch
+        hits_all, kmers_all = [], []
+        t0 = time.perf_counter()
+        for buf, s0, end, fastq in record_chunks(src, self):
+            b = self._parse(buf, s0, end, fastq)
+            if b is None:
+                per_rec_h, per_rec_k = {}, {}
+                for seq, off, rec, _ in self._host_batches(buf, s0, end):
+                    _, h = self.f.query_host(seq, off, want_bits=False)
+                    lens = np.diff(off.astype(np.int64))
+                    for r, hh, L in zip(rec.tolist(), h.tolist(), lens.tolist()):
+                        per_rec_h[r] = per_rec_h.get(r, 0) + hh
+                        per_rec_k[r] = per_rec_k.get(r, 0) + max(0, L - (self.k - 1))
+                n = max(per_rec_h) + 1 if per_rec_h else 0
+                hits_all.append(np.array([per_rec_h.get(r, 0) for r in range(n)], dtype=np.uint64))
+                kmers_all.append(np.array([per_rec_k.get(r, 0) for r in range(n)], dtype=np.uint64))
+                continue
+            seq, off, n_rec = b
+            if self.h_hits.numel() < n_rec + 1:
+                cap = max(n_rec + 1, 2 * self.h_hits.numel())
+                self.h_hits = torch.empty(cap, dtype=torch.int32).pin_memory()
+                self.h_off = torch.empty(cap + 1, dtype=torch.int64).pin_memory()
+            hits = torch.empty(max(n_rec, 1), dtype=torch.int32, device=seq.device)
+            self.f.query(seq, off, hits=hits[:n_rec], want_bits=False, stream=self.stream)
+            with torch.cuda.stream(self.stream):
+                self.h_hits[:n_rec].copy_(hits[:n_rec], non_blocking=True)
+                self.h_off[:n_rec + 1].copy_(off, non_blocking=True)
+            self.stream.synchronize()
+            o = self.h_off[:n_rec + 1].numpy()
+            hits_all.append(self.h_hits[:n_rec].numpy().view(np.uint32).astype(np.uint64))
+            kmers_all.append(np.maximum(np.diff(o) - (self.k - 1), 0).astype(np.uint64))
+            self.stats["records"] += n_rec
+            self.stats["bases"] += seq.numel()
+        self.stats["seconds"] = time.perf_counter() - t0
+        hits = np.concatenate(hits_all) if hits_all else np.zeros(0, np.uint64)
+        kmers = np.concatenate(kmers_all) if kmers_all else np.zeros(0, np.uint64)
+        return hits, kmers, dict(self.stats)

@@ -88,6 +88,8 @@ def load_library() -> ctypes.CDLL:
                                    ctypes.POINTER(ctypes.c_float)]),
             "sbf_probe_sectors": (I, [P, U64, I, U64, U64, I, P, P]),
             "sbf_fastx_create": (I, [I, ctypes.POINTER(P)]),
+            "sbf_fastx_device_scratch": (I, [U64, ctypes.POINTER(U64)]),
+            "sbf_fastx_parse_device": (I, [P, U64, I, P, P, U64, P, U64, P, P]),
             "sbf_fastx_destroy": (None, [P]),
             "sbf_fastx_parse": (I, [P, P, U64, I, P, U64, P, P, U64, ctypes.POINTER(U64),
                                     ctypes.POINTER(U64), ctypes.POINTER(U64)]),
