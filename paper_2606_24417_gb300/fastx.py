@@ -13,10 +13,12 @@ piece repeats its last k-1 bases, so every k-mer is in exactly one piece;
 from __future__ import annotations
 
 import ctypes
+import os
 import queue
 import threading
 import time
 import zlib
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -301,6 +303,33 @@ def record_chunks(src, owner):
     pend = b""  # decompressed bytes not yet placed
     carry = np.zeros(0, dtype=np.uint8)
     first, fastq, i, eof = True, None, 0, False
+    pos = 0  # file offset of the next byte to read (plain files)
+    readers = ThreadPoolExecutor(max_workers=8) if fh is not None else None
+
+    def pread_into(buf, lo, hi):
+        """buf[lo:hi] from the file at `pos`, read by several threads at
+        once (os.preadv releases the GIL); returns the bytes read."""
+        parts = np.linspace(lo, hi, 9).astype(np.int64)
+        jobs = [(int(a), int(b)) for a, b in zip(parts[:-1], parts[1:]) if b > a]
+
+        def one(job):
+            a, b = job
+            got, mv = 0, memoryview(buf)[a:b]
+            while got < b - a:
+                r = os.preadv(fh.fileno(), [mv[got:]], pos + (a - lo) + got)
+                if r == 0:
+                    break
+                got += r
+            return got
+
+        counts = list(readers.map(one, jobs))
+        total = 0
+        for (a, b), c in zip(jobs, counts):  # stop at the first short part (end of file)
+            total += c
+            if c < b - a:
+                break
+        return total
+
     try:
         while not eof or carry.size:
             buf = owner.bufs[i % 2]
@@ -312,10 +341,11 @@ def record_chunks(src, owner):
                 cap = owner.cap
                 while n < cap and not eof:  # fill the rest of the buffer
                     if fh is not None:
-                        got = fh.readinto(memoryview(buf)[n:cap])
-                        if not got:
+                        got = pread_into(buf, n, cap)
+                        if got < cap - n:
                             eof = True
-                        n += got or 0
+                        n += got
+                        pos += got
                     else:
                         if not pend:
                             pend = next(pieces, b"")
@@ -358,6 +388,7 @@ def record_chunks(src, owner):
     finally:
         if fh is not None:
             fh.close()
+            readers.shutdown()
 
 
 class DeviceFastx:
