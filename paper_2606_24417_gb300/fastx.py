@@ -36,7 +36,87 @@ def _host_buffer(n: int, dtype, pinned: bool) -> np.ndarray:
     return np.empty(n, dtype=dtype)
 
 
+def bgzf_blocks(data) -> list | None:
+    """Member boundaries [(start, end), ...] of a BGZF file (gzip members whose
+    header carries the 'BC' extra field with the member size), or None if
+    `data` (a bytes-like object) is not BGZF throughout."""
+    mv = memoryview(data)
+    n, at, out = len(mv), 0, []
+    while at < n:
+        if n - at < 18 or mv[at] != 0x1F or mv[at + 1] != 0x8B or mv[at + 2] != 8 or not (mv[at + 3] & 4):
+            return None
+        xlen = mv[at + 10] | (mv[at + 11] << 8)
+        x, xe, bsize = at + 12, at + 12 + xlen, None
+        while x + 4 <= xe:
+            slen = mv[x + 2] | (mv[x + 3] << 8)
+            if mv[x] == ord("B") and mv[x + 1] == ord("C") and slen == 2:
+                bsize = (mv[x + 4] | (mv[x + 5] << 8)) + 1
+            x += 4 + slen
+        if bsize is None or at + bsize > n:
+            return None
+        out.append((at, at + bsize))
+        at += bsize
+    return out
+
+
+def write_bgzf(data: bytes, level: int = 1, block: int = 65280) -> bytes:
+    """BGZF encoding of `data`: gzip members of at most `block` input bytes,
+    each header carrying the 'BC' extra field with the member size, and the
+    empty end-of-file member (the SAM/BAM specification's layout)."""
+    import struct
+
+    def member(chunk: bytes, comp: bytes) -> bytes:
+        bsize = 18 + len(comp) + 8
+        hdr = (b"\x1f\x8b\x08\x04" + b"\0\0\0\0" + b"\0\xff" + struct.pack("<H", 6) + b"BC" +
+               struct.pack("<HH", 2, bsize - 1))
+        return hdr + comp + struct.pack("<II", zlib.crc32(chunk) & 0xFFFFFFFF, len(chunk) & 0xFFFFFFFF)
+
+    out = []
+    for i in range(0, len(data), block):
+        chunk = bytes(data[i:i + block])
+        c = zlib.compressobj(level, zlib.DEFLATED, -15)
+        out.append(member(chunk, c.compress(chunk) + c.flush()))
+    c = zlib.compressobj(level, zlib.DEFLATED, -15)
+    out.append(member(b"", c.compress(b"") + c.flush()))
+    return b"".join(out)
+
+
+def _inflate_group(data, blocks):
+    return b"".join(zlib.decompress(bytes(data[a:b]), 31) for a, b in blocks)
+
+
 def text_chunks(src, chunk_bytes: int = 16 << 20):
+    """Decompressed text of a path, bytes or file object, in chunks.  BGZF
+    input is inflated by several threads at once (zlib releases the GIL),
+    other gzip input member by member on one thread."""
+    if isinstance(src, str):
+        with open(src, "rb") as fh:
+            head = fh.read(4)
+        if head[:2] == _GZIP_MAGIC and len(head) == 4 and head[3] & 4:
+            import mmap
+
+            with open(src, "rb") as fh, mmap.mmap(fh.fileno(), 0, access=mmap.ACCESS_READ) as mm:
+                blocks = bgzf_blocks(mm)
+                if blocks:
+                    yield from _bgzf_text(mm, blocks)
+                    return
+    elif isinstance(src, (bytes, bytearray, memoryview)) and bytes(src[:2]) == _GZIP_MAGIC:
+        blocks = bgzf_blocks(src)
+        if blocks:
+            yield from _bgzf_text(src, blocks)
+            return
+    yield from _serial_text_chunks(src, chunk_bytes)
+
+
+def _bgzf_text(data, blocks, group: int = 256, workers: int = 16):
+    groups = [blocks[i:i + group] for i in range(0, len(blocks), group)]
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        for piece in ex.map(lambda g: _inflate_group(data, g), groups):
+            if piece:
+                yield piece
+
+
+def _serial_text_chunks(src, chunk_bytes: int = 16 << 20):
     """Decompressed text of a path, bytes or file object, in chunks."""
     if isinstance(src, (bytes, bytearray, memoryview)):
         data = bytes(src)
