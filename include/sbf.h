@@ -143,6 +143,12 @@ int sbf_clear(sbf_filter* f, sbf_stream_t stream);
  * synchronous.  This is also the checkpoint format's payload. */
 int sbf_get_bits(const sbf_filter* f, uint64_t* h_words);
 int sbf_set_bits(sbf_filter* f, const uint64_t* h_words);
+/* Device-to-device copy of the filter's words [word_begin, word_begin +
+ * n_words) to d_words (to_filter = 0) or from it (to_filter = 1), on
+ * `stream`.  Used to combine filters that inserted disjoint read sets: the
+ * filter after inserting everything is the OR of their words (Alg. 1). */
+int sbf_copy_bits_device(sbf_filter* f, uint64_t* d_words, uint64_t word_begin, uint64_t n_words,
+                         int to_filter, sbf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Insert and query (Alg. 1 and Alg. 2).  Device pointers.

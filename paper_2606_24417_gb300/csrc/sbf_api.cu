@@ -243,6 +243,23 @@ int sbf_set_bits(sbf_filter* f, const uint64_t* h_words) {
   return e == cudaSuccess ? SBF_OK : cuda_fail(e, "set_bits");
 }
 
+int sbf_copy_bits_device(sbf_filter* f, uint64_t* d_words, uint64_t word_begin, uint64_t n_words,
+                         int to_filter, sbf_stream_t stream) {
+  clear_error();
+  if (!f || (n_words && !d_words)) return fail(SBF_EINVAL, "NULL argument");
+  if (word_begin > f->n_words || n_words > f->n_words - word_begin)
+    return fail(SBF_EINVAL, "words [%llu, %llu) outside the filter's %llu",
+                (unsigned long long)word_begin, (unsigned long long)(word_begin + n_words),
+                (unsigned long long)f->n_words);
+  if (n_words == 0) return SBF_OK;
+  DeviceGuard dg(f->device);
+  uint64_t* fw = f->geom.words + word_begin;
+  cudaError_t e = to_filter
+      ? cudaMemcpyAsync(fw, d_words, n_words * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream)
+      : cudaMemcpyAsync(d_words, fw, n_words * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+  return e == cudaSuccess ? SBF_OK : cuda_fail(e, "copy_bits_device");
+}
+
 int sbf_insert_seqs(sbf_filter* f, const uint8_t* d_seq, uint64_t seq_len, const uint64_t* d_off,
                     uint64_t n_reads, sbf_stream_t stream) {
   clear_error();

@@ -59,6 +59,7 @@ def load_library() -> ctypes.CDLL:
             "sbf_kernel_variant": (I, [P]),
             "sbf_clear": (I, [P, P]),
             "sbf_get_bits": (I, [P, P]),
+            "sbf_copy_bits_device": (I, [P, P, U64, U64, I, P]),
             "sbf_set_bits": (I, [P, P]),
             "sbf_insert_seqs": (I, [P, P, U64, P, U64, P]),
             "sbf_query_seqs": (I, [P, P, U64, P, U64, U32P, U32P, P]),
@@ -244,6 +245,13 @@ class SuperBloomFilter:
         out = np.empty(self.n_words, dtype=np.uint64)
         _check(self._lib.sbf_get_bits(self._h, _host_ptr(out)))
         return out
+
+    def copy_words_device(self, dst, word_begin: int = 0, to_filter: bool = False,
+                          stream=None) -> None:
+        """Copy words [word_begin, word_begin + dst.numel()) of the filter to
+        the int64 CUDA tensor dst (or from it into the filter)."""
+        _check(self._lib.sbf_copy_bits_device(self._h, _dev_ptr(dst, 8), word_begin, dst.numel(),
+                                              1 if to_filter else 0, _stream_handle(stream)))
 
     def set_words(self, w: np.ndarray) -> None:
         w = np.ascontiguousarray(w, dtype=np.uint64)

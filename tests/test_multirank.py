@@ -46,3 +46,52 @@ def test_single_rank_is_identity():
     import bench
 
     assert bench.max_over_ranks([1.5, 2.5]) == [1.5, 2.5]
+
+
+def _or_worker(rank, world, port, out, genome_path, params):
+    import numpy as np
+    import torch.distributed as dist
+
+    from oracle import OracleSBF
+    from paper_2606_24417_gb300.dist import allreduce_or_array, read_share
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        data = np.load(genome_path)
+        seq, off = data["seq"], data["off"]
+        r0, r1 = read_share(off, rank, world)
+        o = OracleSBF(*params)
+        a, b = int(off[r0]), int(off[r1])
+        o.insert(seq[a:b], off[r0:r1 + 1] - off[r0])   # this rank's share only
+        out[rank] = (r0, r1, allreduce_or_array(o.words()).tobytes())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_distributed_insert_or_allreduce_two_gloo_ranks(tmp_path):
+    """Two ranks insert disjoint read shares into their own filters; one OR
+    all-reduce gives both the filter of all reads (Alg. 1: insertion is the
+    OR of the inserted bits)."""
+    import numpy as np
+    import torch.multiprocessing as mp
+
+    from oracle import OracleSBF
+    from paper_2606_24417_gb300 import synth
+
+    g = synth.bacterial_genome(400_000, seed=5)
+    seq, off = synth.sample_reads(g, 3000, 150, 0.01, seed=6)
+    p = str(tmp_path / "reads.npz")
+    np.savez(p, seq=seq, off=off)
+    params = (31, 16, 28, 4, 1 << 22)
+    port = _free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_or_worker, args=(2, port, out, p, params), nprocs=2, join=True)
+        res = dict(out)
+    full = OracleSBF(*params)
+    full.insert(seq, off)
+    want = full.words().tobytes()
+    assert res[0][2] == want and res[1][2] == want
+    assert res[0][0] == 0 and res[0][1] == res[1][0] and res[1][1] == off.size - 1
