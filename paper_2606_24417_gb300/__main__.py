@@ -62,20 +62,25 @@ def _parser() -> argparse.ArgumentParser:
     return ap
 
 
-def _insert(f, path, host_parse):
-    from .fastx import DeviceFastx, insert_fastx
+class _Files:
+    """Inserts or queries files through one device pipeline (its pinned and
+    device buffers are allocated once), or through the host parser."""
 
-    if host_parse or f.alphabet == 2:
-        return insert_fastx(f, path)
-    return DeviceFastx(f).insert(path)
+    def __init__(self, f, host_parse: bool):
+        from .fastx import DeviceFastx
 
+        self.f = f
+        self.dev = None if host_parse or f.alphabet == 2 else DeviceFastx(f)
 
-def _query(f, path, host_parse):
-    from .fastx import DeviceFastx, query_fastx
+    def insert(self, path):
+        from .fastx import insert_fastx
 
-    if host_parse or f.alphabet == 2:
-        return query_fastx(f, path)
-    return DeviceFastx(f).query(path)
+        return insert_fastx(self.f, path) if self.dev is None else self.dev.insert(path)
+
+    def query(self, path):
+        from .fastx import query_fastx
+
+        return query_fastx(self.f, path) if self.dev is None else self.dev.query(path)
 
 
 def main(argv=None) -> int:
@@ -88,8 +93,9 @@ def main(argv=None) -> int:
                              layout=LAYOUT_PAPER if args.layout == "paper" else LAYOUT_DEFAULT,
                              alphabet=args.alphabet)
         t = time.perf_counter()
+        files = _Files(f, args.host_parse)
         for path in args.inputs:
-            _insert(f, path, args.host_parse)
+            files.insert(path)
         f.save(args.out)
         print(f"{args.out}: {len(args.inputs)} file(s) inserted in {time.perf_counter() - t:.2f} s, "
               f"{f.n_shards} shards of {f.shard_bits} bits", file=sys.stderr)
@@ -105,8 +111,9 @@ def main(argv=None) -> int:
     out = sys.stdout if args.out == "-" else open(args.out, "w")
     try:
         out.write("file\trecord\tpositive_kmers\tkmers\tfraction\n")
+        files = _Files(f, args.host_parse)
         for path in args.inputs:
-            hits, kmers, _ = _query(f, path, args.host_parse)
+            hits, kmers, _ = files.query(path)
             frac = np.divide(hits, kmers, out=np.zeros(hits.size, dtype=np.float64), where=kmers > 0)
             keep = np.arange(hits.size) if args.min_frac is None else np.flatnonzero(frac >= args.min_frac)
             for r in keep.tolist():

@@ -495,6 +495,10 @@ class DeviceFastx:
         self.h_off = torch.empty(0, dtype=torch.int64)   # pinned, grown on demand
         self.h_hits = torch.empty(0, dtype=torch.int32)
         self.result = (ctypes.c_uint64 * 3)()
+        self._reset()
+
+    def _reset(self) -> None:
+        """Statistics of one insert or query call."""
         self.stats = {"chunks": 0, "host_fallback_chunks": 0, "records": 0, "bases": 0,
                       "text_bytes": 0, "seconds": 0.0}
 
@@ -543,6 +547,7 @@ class DeviceFastx:
             yield seq, off, rec, rd
 
     def insert(self, src) -> dict:
+        self._reset()
         t0 = time.perf_counter()
         for buf, s0, end, fastq in record_chunks(src, self):
             b = self._parse(buf, s0, end, fastq)
@@ -562,6 +567,7 @@ class DeviceFastx:
     def query(self, src):
         """Per-record positive k-mers and k-mer positions (as query_fastx)."""
         torch = self._torch
+        self._reset()
         hits_all, kmers_all = [], []
         t0 = time.perf_counter()
         for buf, s0, end, fastq in record_chunks(src, self):
