@@ -895,8 +895,16 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
 
 }
 
+// Blocks per SM the register budget is sized for: four (128 registers) in
+// general; three (up to 168, no spills) for 64-bit order keys where that
+// measured faster -- inserts, and queries on 512-bit shards.
+template <bool KEY64, bool INSERT, int B>
+constexpr int min_blocks() {
+  return (KEY64 && (INSERT || B == 512)) ? 3 : 4;
+}
+
 template <int W, int H, int B, bool KEY64, bool INSERT>
-__global__ void __launch_bounds__(kThreads, 4) fused_kernel(Params P) {
+__global__ void __launch_bounds__(kThreads, min_blocks<KEY64, INSERT, B>()) fused_kernel(Params P) {
   using Sm = WarpSmem<H, B, KEY64>;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   Sm& S = reinterpret_cast<Sm*>(smem_raw)[threadIdx.x >> 5];
