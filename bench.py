@@ -1178,6 +1178,92 @@ def run_fpr_curve(args):
     return 0
 
 
+def run_filter_sizes(args):
+    """The bacterial workload (100 Mbp genome inserted, 20M 150 bp reads
+    queried; k=31, m=16, s=28, H=4, 512-bit shards) on filters of 8 MiB to
+    4 GiB: inside the 129 MB L2, around it and far beyond it.  Each size is
+    set against its own random-sector roofline: streamed bytes at the copy
+    peak plus one shard per super-k-mer run at the probe's measured rate
+    over a buffer of the filter's size (served from L2 when it fits)."""
+    import torch
+
+    from paper_2606_24417_gb300 import build_lib
+    from paper_2606_24417_gb300.sbf import SuperBloomFilter
+
+    build_lib.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    genome, reads, roff = make_workload(0, small=args.case == "small")
+    n_reads = roff.size - 1
+    ins_kmers = genome.size - K + 1
+    q_kmers = n_reads * (READ_LEN - K + 1)
+    d_genome = torch.from_numpy(genome).to(dev)
+    d_goff = torch.tensor([0, genome.size], dtype=torch.int64, device=dev)
+    d_reads = torch.from_numpy(reads).to(dev)
+    d_roff = torch.from_numpy(roff.astype(np.int64)).to(dev)
+    d_bits = torch.empty((reads.size + 31) // 32, dtype=torch.int32, device=dev)
+    d_hits = torch.empty(n_reads, dtype=torch.int32, device=dev)
+    stats = torch.zeros(3, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peak, peak_kind = measured_peaks()
+    sector_b = SHARD_BITS // 8
+    rows = []
+    for e in (26, 27, 28, 29, 30, 31, 32, 33, 35):
+        f = SuperBloomFilter(K, M, S, H, 1 << e, shard_bits=SHARD_BITS)
+        # runs (one shard each) of the query and of the insert
+        stats.zero_()
+        f.insert(d_genome, d_goff)
+        f.query(d_reads, d_roff, bits=d_bits, hits=d_hits, stats=stats)
+        torch.cuda.synchronize()
+        runs_q = int(stats[1].item())
+        stats.zero_()
+        f.query(d_genome, d_goff, want_bits=False, want_hits=False, stats=stats)
+        torch.cuda.synchronize()
+        runs_i = int(stats[1].item())
+        t_i, t_q = [], []
+        for rep in range(3 + max(args.steps, 3)):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            flush.fill_(1)
+            f.clear()
+            ev[0].record(stream)
+            f.insert(d_genome, d_goff)
+            ev[1].record(stream)
+            f.query(d_reads, d_roff, bits=d_bits, hits=d_hits)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            if rep >= 3:
+                t_i.append(ev[0].elapsed_time(ev[1]))
+                t_q.append(ev[1].elapsed_time(ev[2]))
+        ins_ms, q_ms = statistics.median(t_i), statistics.median(t_q)
+        fbytes = f.nbytes
+        g_gbs = sector_bandwidth(dev, stream, fbytes, sector_b, False, 1 << 27)
+        r_gbs = sector_bandwidth(dev, stream, fbytes, sector_b, True, 1 << 25)
+        q_stream = reads.nbytes + roff.nbytes + (reads.size + 7) // 8 + 4 * n_reads
+        q_bound = q_kmers / (q_stream / (peak * 1e9) + runs_q * sector_b / (g_gbs * 1e9))
+        i_bound = ins_kmers / (genome.nbytes / (peak * 1e9) + runs_i * 2 * sector_b / (r_gbs * 1e9))
+        q_rate, i_rate = q_kmers / (q_ms / 1e3), ins_kmers / (ins_ms / 1e3)
+        rows.append({"log2_bits": e, "filter_bytes": fbytes, "in_l2": fbytes <= (96 << 20),
+                     "insert_ms": ins_ms, "query_ms": q_ms,
+                     "insert_kmers_per_s": i_rate, "query_kmers_per_s": q_rate,
+                     "probe_gather_gbs": g_gbs, "probe_rmw_gbs": r_gbs,
+                     "query_sector_bound": q_bound, "insert_sector_bound": i_bound,
+                     "query_frac": q_rate / q_bound, "insert_frac": i_rate / i_bound,
+                     "positive_kmers": int(d_hits.sum().item())})
+        log(f"[bench] 2^{e} bits: query {q_rate / 1e9:.1f} G/s ({q_rate / q_bound:.2f} of bound), "
+            f"insert {i_rate / 1e9:.1f} G/s ({i_rate / i_bound:.2f})")
+        f.close()
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    with open(os.path.join(ROOT, "gpurun_out", "filter_sizes.json"), "w") as fh:
+        json.dump(rows, fh)
+    print(json.dumps({"workload": "filter_sizes: 100 Mbp bacterial-shaped genome inserted, "
+                      f"{n_reads} 150 bp reads queried (half sampled with 1% errors, half random), "
+                      "k=31 m=16 s=28 H=4, 512-bit shards, filters of 2^26..2^35 bits; "
+                      "256 MB L2 flush before each timed step",
+                      "peak_gbs": peak, "peak_kind": peak_kind, "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1188,7 +1274,7 @@ def main():
                     help="small: 2M query reads (300 MB, still larger than L2) for profiling")
     ap.add_argument("--workload", default="bacterial",
                     choices=["bacterial", "batched", "served", "sweep", "paper_sweep", "fastx",
-                             "alphabets", "fpr_curve"],
+                             "alphabets", "fpr_curve", "filter_sizes"],
                     help="batched: the many-filter workload (its own JSON line)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="device-timed steps only (no e2e, no CPU baseline): profiling runs")
@@ -1215,6 +1301,8 @@ def main():
         return run_alphabets(args) if rank == 0 else 0
     if args.workload == "fpr_curve":
         return run_fpr_curve(args) if rank == 0 else 0
+    if args.workload == "filter_sizes":
+        return run_filter_sizes(args) if rank == 0 else 0
     if world > 1:
         import torch
         import torch.distributed as dist
