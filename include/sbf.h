@@ -136,6 +136,16 @@ const uint64_t* sbf_device_words(const sbf_filter* f);
  * one-k-mer-per-thread kernels.  Both give identical bits. */
 int sbf_kernel_variant(const sbf_filter* f);
 
+/* Device status of the filter's kernels: *status = 0 while every launch ran
+ * to completion.  The fused query waits on a shard-copy barrier (filters of
+ * 1 GiB and more); a wait bounded at one second of the GPU's global timer
+ * that ran out sets bit 0, and that warp stopped early, so answers of the
+ * launches since the last clear are incomplete.  Batched and served launches
+ * report to the first filter of their batch or to their filter.  Reads the
+ * word (synchronous, after the work queued before on any stream has been
+ * ordered by the caller); clear != 0 resets it.  SBF_EINVAL on NULL. */
+int sbf_device_status(const sbf_filter* f, uint32_t* status, int clear);
+
 /* Zero all bits (stream-ordered). */
 int sbf_clear(sbf_filter* f, sbf_stream_t stream);
 

@@ -150,12 +150,17 @@ int sbf_create_full(int k, int m, int s, int H, uint64_t bits, int shard_bits, i
                 (unsigned long long)(n_words * 8), cudaGetErrorString(e));
   }
   e = cudaMemset(words, 0, n_words * sizeof(uint64_t));
+  uint32_t* status = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(status, 0, sizeof(uint32_t));
   if (e != cudaSuccess) {
+    cudaFree(status);
     cudaFree(words);
     delete f;
-    return cuda_fail(e, "cudaMemset");
+    return cuda_fail(e, "filter allocation");
   }
   f->geom = make_geom(words, n_shards, k, m, s, H, shard_bits, canonical ? 1 : 0, layout, alphabet);
+  f->geom.status = status;
   f->n_words = n_words;
   f->fused = fused_supported(f->geom);
   *out = f;
@@ -191,6 +196,7 @@ void sbf_destroy(sbf_filter* f) {
     cudaFree(f->host_dev_hits[i]);
   }
   cudaFree(f->geom.words);
+  cudaFree(f->geom.status);
   cudaFreeHost(f->host_first);
   for (int i = 0; i < 2; ++i) {
     cudaFreeHost(f->host_stage_bits[i]);
@@ -214,6 +220,15 @@ int sbf_info(const sbf_filter* f, int* k, int* m, int* s, int* H, int* shard_bit
 }
 
 uint64_t sbf_num_words(const sbf_filter* f) { return f ? f->n_words : 0; }
+
+int sbf_device_status(const sbf_filter* f, uint32_t* status, int clear) {
+  clear_error();
+  if (!f || !status) return fail(SBF_EINVAL, "NULL argument");
+  DeviceGuard dg(f->device);
+  cudaError_t e = cudaMemcpy(status, f->geom.status, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && clear && *status) e = cudaMemset(f->geom.status, 0, sizeof(uint32_t));
+  return e == cudaSuccess ? SBF_OK : cuda_fail(e, "device_status");
+}
 
 int sbf_kernel_variant(const sbf_filter* f) { return f && f->fused ? 1 : 0; }
 
@@ -528,6 +543,7 @@ int host_run_fused(sbf_filter* f, bool is_query, const uint8_t* h_seq, const uin
     P.work = nullptr;
     P.chunk = 1;
     P.grid_blocks = 0;
+    P.big = fused::is_big(f->geom) ? 1u : 0u;
     if ((e = fused::launch_params(P, !is_query, st)) != cudaSuccess) return cuda_fail(e, "host path launch");
     uint32_t* hits_dst = stage_hits ? f->host_stage_hits[b] : h_hits + c.r0;
     uint32_t* bits_dst = stage_bits ? f->host_stage_bits[b] + 1 : h_bits + c.a / 32 + 1;

@@ -22,6 +22,7 @@ using sbf::fused::Segment;
 struct sbf_batch {
   std::vector<sbf_filter*> filters;
   sbf::Geom geom{};
+  bool big = false;  // some filter has the bulk-copy size (its queries take the BULK kernels)
   int device = 0;
   Segment* d_segs = nullptr;
   Segment* h_segs = nullptr;  // pinned staging of the table
@@ -178,6 +179,7 @@ cudaError_t enqueue_fused(sbf_batch* b, bool insert, const uint8_t* seq, uint64_
   P.work = sc.dynamic ? b->d_work : nullptr;
   P.chunk = sc.chunk > 0 ? sc.chunk : 1;
   P.grid_blocks = sc.grid_blocks;
+  P.big = b->big ? 1u : 0u;
   return sbf::fused::launch_params(P, insert, st);
 }
 
@@ -214,6 +216,7 @@ int run_batch(sbf_batch* b, bool insert, const uint8_t* d_seq, uint64_t seq_len,
       P.iters = s.iters;
       P.work = nullptr;
       P.chunk = 1;
+      P.big = s.n_shards * (uint64_t)(b->geom.shard_bits / 8) >= sbf::fused::kTmaMinBytes ? 1u : 0u;
       if ((e = sbf::fused::launch_params(P, insert, st)) != cudaSuccess)
         return cuda_fail(e, "per-filter launch");
     }
@@ -295,6 +298,7 @@ int sbf_batch_create(sbf_filter* const* filters, int n_filters, sbf_batch** out)
   if (!b) return fail(SBF_ENOMEM, "host allocation failed");
   b->filters.assign(filters, filters + n_filters);
   b->geom = g0;
+  for (int i = 0; i < n_filters; ++i) b->big = b->big || sbf::fused::is_big(filters[i]->geom);
   b->device = filters[0]->device;
   DeviceGuard dg(b->device);
   if (cudaMalloc(&b->d_work, sizeof(unsigned long long)) != cudaSuccess ||

@@ -40,6 +40,7 @@ struct Geom {
   int sector_bits;     // B / S
   int sector_log2;     // b = log2(B / S)
   int slice;           // q = floor(64 / H)
+  uint32_t* status;    // device word: nonzero after a kernel stopped on a timed-out wait, or NULL
 };
 
 // Layout 1 is Sec. IV-B and Alg. 1/2 taken literally: 2^P shards (the caller
@@ -72,6 +73,7 @@ __host__ __device__ inline Geom make_geom(uint64_t* words, uint64_t n_shards, in
   while ((1 << b) < g.sector_bits) ++b;
   g.sector_log2 = b;
   g.slice = 64 / H;
+  g.status = nullptr;
   return g;
 }
 

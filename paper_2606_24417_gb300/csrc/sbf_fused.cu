@@ -45,6 +45,7 @@ static Params single(const Geom& g, const uint8_t* seq, uint64_t seq_len, const 
   P.work = nullptr;
   P.chunk = 1;
   P.grid_blocks = 0;
+  P.big = is_big(g) ? 1u : 0u;
   return P;
 }
 

@@ -20,7 +20,8 @@
 //    modular inverse -- no argmin is tracked.
 //  * Runs (super-k-mers, Sec. II-B): run heads are compacted warp-wide into
 //    slots; the shard of each run is computed once and loaded once into
-//    shared memory with cp.async (query), or zeroed there (insert).
+//    shared memory (query: cp.async, and for filters of 1 GiB or more partly
+//    TMA bulk copies on a per-warp mbarrier), or zeroed there (insert).
 //  * Findere with pair deduplication: k-mer j needs its k-s+1 s-mers tested
 //    in its run's shard.  Every position t tests its own pair (t, shard(t));
 //    every run end e adds the z = k-s pairs (e+d, shard(e)).  A word-parallel
@@ -45,6 +46,21 @@ constexpr int kThreads = 32 * kWarps;
 constexpr int kSlotCap = 64;        // runs per iteration with a shard copy in shared memory
 constexpr int kStage = 34;          // staged 16-base words per iteration (544 bases)
 constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Shard copies of the query.  Below kTmaMinBytes of filter every slot is
+// loaded with 16-byte cp.async.  From there on, slots kTmaFromSlot.. are
+// loaded by the TMA engine instead (one cp.async.bulk of B/8 bytes each,
+// completing on the warp's mbarrier): beyond L2 nearly every cp.async misses
+// L2 and the TLB and holds the load/store pipe that all shared-memory loads
+// and shuffles of the SM also use (short-scoreboard stalls tripled on a
+// 2 GiB filter), while the bulk copies' fixed cost makes them slower than
+// cp.async on filters that L2 serves.  Measured on GB300 (2M reads, k=31,
+// m=16, s=28, H=4, 512-bit shards): 4 GiB 2.99 -> 2.49 ms, 1 GiB 2.57 ->
+// 2.42 ms, 512 MiB 2.27 -> 2.40 ms; so the switch is at 1 GiB.
+constexpr uint64_t kTmaMinBytes = 1ull << 30;
+constexpr uint32_t kTmaFromSlot = 32;
+// Bound of every wait on that barrier: one second of the global timer.
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
 
 // Modular inverses of the odd golden-ratio multipliers (Newton iteration).
 __host__ __device__ constexpr uint32_t inv32(uint32_t a) {
@@ -199,6 +215,7 @@ struct Params {
   unsigned long long* work;  // dynamic scheduling counter (zeroed), or NULL for a static split
   uint32_t chunk;         // iterations per dynamically claimed work item
   uint32_t grid_blocks;   // blocks to launch (0: enough for the work, capped at full occupancy)
+  uint32_t big;           // a segment's filter has kTmaMinBytes or more (query: BULK kernels)
 };
 
 template <int H, int B, bool KEY64>
@@ -225,7 +242,26 @@ struct alignas(16) WarpSmem {
   uint32_t kill_w[17];
   uint32_t k_w[17];
   uint32_t pref_w[17];
+  unsigned long long bar;                // query: the shard copies' mbarrier
 };
+
+// Waits for the completion of phase `parity` of the mbarrier at shared
+// address bar, at most kWaitLimitNs of the global timer; false if it did not
+// complete in that time.
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity) {
+  uint64_t t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > kWaitLimitNs) return false;
+  }
+}
 
 __device__ __forceinline__ uint32_t pairswap(uint32_t x) {
   return ((x >> 1) & 0x55555555u) | ((x & 0x55555555u) << 1);
@@ -324,13 +360,15 @@ __device__ bool prev_kmer_key(const Geom& g, const uint8_t* seq, uint64_t seq_le
   return true;
 }
 
-// Iterations [it0, it1) of one segment, walked by one warp.
-template <int W, int H, int B, bool KEY64, bool INSERT>
-__device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params& P,
+// Iterations [it0, it1) of one segment, walked by one warp.  False if a
+// wait for shard copies ran out (the filter's status word is set).  BULK:
+// the kernel variant for launches with a filter of kTmaMinBytes or more.
+template <int W, int H, int B, bool KEY64, bool INSERT, bool BULK>
+__device__ __forceinline__ bool run_range(WarpSmem<H, B, KEY64>& S, const Params& P,
                                           const Segment& seg, uint64_t it0, uint64_t it1,
                                           int lane, unsigned long long& st_valid,
                                           unsigned long long& st_runs,
-                                          unsigned long long& st_pos) {
+                                          unsigned long long& st_pos, uint32_t& bar_phase) {
   using L = Layout<H, B>;
   using Pack = typename L::Pack;
   using KeyT = typename std::conditional<KEY64, uint64_t, uint32_t>::type;
@@ -638,6 +676,21 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
     // ---------------- shards of the runs: index, then async copy ----------
     const uint64_t n_shards = g.n_shards;
     const bool masked = g.layout == 1;  // the paper's shard rule: key & (2^P - 1)
+    // slots [kTmaFromSlot, min(total, kSlotCap)) of a large filter go to the TMA engine
+    const uint32_t n_copy = total_slots < (uint32_t)kSlotCap ? total_slots : (uint32_t)kSlotCap;
+    uint32_t n_bulk = 0;
+    if constexpr (BULK)
+      n_bulk = (n_shards * (uint64_t)(B / 8) >= kTmaMinBytes && n_copy > kTmaFromSlot)
+                   ? n_copy - kTmaFromSlot : 0u;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&S.bar);
+    if (BULK && n_bulk) {
+      // this lane's earlier generic accesses of the slots precede the bulk writes
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      if (lane == 0)
+        asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
+                     ::"r"(bar), "r"(n_bulk * (uint32_t)(B / 8)) : "memory");
+      __syncwarp();
+    }
     for (uint32_t si = lane; si < total_slots; si += 32) {
       uint64_t x;
       if (masked) {
@@ -660,10 +713,16 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
         } else {
           const uint8_t* src = reinterpret_cast<const uint8_t*>(g.words) + x * (uint64_t)(B / 8);
           uint32_t dst = (uint32_t)__cvta_generic_to_shared(&S.shard[si * L::SLOT]);
+          if (BULK && n_bulk && si >= kTmaFromSlot) {  // 16-byte aligned, B/8 a multiple of 16
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                ::"r"(dst), "l"(src), "n"(B / 8), "r"(bar) : "memory");
+          } else {
 #pragma unroll
-          for (int c = 0; c < B / 128; ++c)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16 * c),
-                         "l"(src + 16 * c));
+            for (int c = 0; c < B / 128; ++c)
+              asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16 * c),
+                           "l"(src + 16 * c));
+          }
         }
       }
     }
@@ -696,6 +755,15 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
       S.hs[j * HS + lane] = make_pack<H, B>(x);
     }
     if constexpr (!INSERT) asm volatile("cp.async.wait_group 0;\n" ::);
+    if (BULK && n_bulk) {
+      if (!__all_sync(kFull, wait_phase(bar, bar_phase))) {
+        // give up: record it, let copies still in flight land (bounded), stop
+        if (lane == 0 && g.status) atomicOr(g.status, 1u);
+        wait_phase(bar, bar_phase);
+        return false;
+      }
+      bar_phase ^= 1u;
+    }
     __syncwarp();
 
     // ---------------- pair tests / sets ------------------------------------
@@ -892,7 +960,7 @@ __device__ __forceinline__ void run_range(WarpSmem<H, B, KEY64>& S, const Params
     e_batch = e_next;
     __syncwarp();
   }
-
+  return true;
 }
 
 // Blocks per SM the register budget is sized for: four (128 registers) in
@@ -903,13 +971,24 @@ constexpr int min_blocks() {
   return (KEY64 && (INSERT || B == 512)) ? 3 : 4;
 }
 
-template <int W, int H, int B, bool KEY64, bool INSERT>
+template <int W, int H, int B, bool KEY64, bool INSERT, bool BULK>
 __global__ void __launch_bounds__(kThreads, min_blocks<KEY64, INSERT, B>()) fused_kernel(Params P) {
+  static_assert(!(INSERT && BULK), "bulk shard copies are a query variant");
   using Sm = WarpSmem<H, B, KEY64>;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   Sm& S = reinterpret_cast<Sm*>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   unsigned long long st_valid = 0, st_runs = 0, st_pos = 0;
+  uint32_t bar_phase = 0;  // phase of the warp's shard-copy barrier
+  bool alive = true;       // false once a wait ran out
+  if constexpr (BULK) {
+    if (lane == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(&S.bar)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncwarp();
+  }
 
   // Walk global iterations [a, b): split them at segment boundaries.
   auto walk = [&](uint64_t a, uint64_t b) {
@@ -926,9 +1005,12 @@ __global__ void __launch_bounds__(kThreads, min_blocks<KEY64, INSERT, B>()) fuse
       const Segment seg = P.segs ? P.segs[si] : P.seg0;
       const uint64_t s_end = seg.iter_begin + seg.iters;
       const uint64_t e = b < s_end ? b : s_end;
-      if (a < e)
-        run_range<W, H, B, KEY64, INSERT>(S, P, seg, a - seg.iter_begin, e - seg.iter_begin, lane,
-                                          st_valid, st_runs, st_pos);
+      if (a < e && !run_range<W, H, B, KEY64, INSERT, BULK>(S, P, seg, a - seg.iter_begin,
+                                                      e - seg.iter_begin, lane, st_valid, st_runs,
+                                                      st_pos, bar_phase)) {
+        alive = false;
+        return;
+      }
       a = e > a ? e : a;
       if (a >= s_end) ++si;
       if (P.segs == nullptr || si >= P.n_segs) break;
@@ -945,7 +1027,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<KEY64, INSERT, B>()) fuse
     if (a < b) walk(a, b);
   } else {
     // dynamic: claim chunks of iterations from a global counter
-    while (true) {
+    while (alive) {
       uint64_t start = 0;
       if (lane == 0) start = (uint64_t)atomicAdd(P.work, (unsigned long long)P.chunk);
       start = __shfl_sync(kFull, start, 0);
@@ -955,6 +1037,12 @@ __global__ void __launch_bounds__(kThreads, min_blocks<KEY64, INSERT, B>()) fuse
     }
   }
 
+  if constexpr (BULK) {
+    __syncwarp();
+    if (alive && lane == 0)
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(&S.bar)) : "memory");
+  }
   if (!INSERT && P.stats) {
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) {
@@ -970,9 +1058,9 @@ __global__ void __launch_bounds__(kThreads, min_blocks<KEY64, INSERT, B>()) fuse
   }
 }
 
-template <int W, int H, int B, bool KEY64, bool INSERT>
+template <int W, int H, int B, bool KEY64, bool INSERT, bool BULK = false>
 cudaError_t launch(const Params& P, cudaStream_t st) {
-  auto kern = fused_kernel<W, H, B, KEY64, INSERT>;
+  auto kern = fused_kernel<W, H, B, KEY64, INSERT, BULK>;
   constexpr size_t smem = sizeof(WarpSmem<H, B, KEY64>) * kWarps;
   static int blocks_per_sm = 0;  // per instantiation; same on every GB300
   if (blocks_per_sm == 0) {
@@ -991,6 +1079,11 @@ cudaError_t launch(const Params& P, cudaStream_t st) {
   if (grid < 1) grid = 1;
   kern<<<grid, kThreads, smem, st>>>(P);
   return cudaGetLastError();
+}
+
+// True if a filter has kTmaMinBytes or more (its queries take the BULK kernels).
+inline bool is_big(const Geom& g) {
+  return g.n_shards * (uint64_t)(g.shard_bits / 8) >= kTmaMinBytes;
 }
 
 // Launch a prepared parameter block (dispatch over the compiled grid).

@@ -155,6 +155,9 @@ extern "C" int sbf_batch_query_noalloc(sbf_filter* const* filters, int n_filters
   P.work = d_work;
   P.chunk = 64;
   P.grid_blocks = 0;
+  P.big = 0;
+  for (int i = 0; i < n_filters; ++i)
+    if (sbf::fused::is_big(filters[i]->geom)) P.big = 1;
   e = sbf::fused::launch_params(P, false, st);
   return e == cudaSuccess ? SBF_OK : cuda_fail(e, "batched launch");
 }

@@ -211,6 +211,7 @@ int start_launch(sbf_server* s, Launch& L) {
   P.work = nullptr;
   P.chunk = 1;
   P.grid_blocks = 0;
+  P.big = sbf::fused::is_big(g) ? 1u : 0u;
   if ((e = sbf::fused::launch_params(P, false, st)) != cudaSuccess) return cuda_fail(e, "server launch");
   for (Request* r : L.reqs) {
     const uint64_t hits_at = r->meta_at + (r->n_reads + 1) * 8;
@@ -373,6 +374,7 @@ int sbf_server_create(const sbf_filter* f, uint64_t read_budget_bytes, int max_i
   if (ok) {
     Params P{};
     P.g = f->geom;
+    P.big = sbf::fused::is_big(f->geom) ? 1u : 0u;
     ok = sbf::fused::launch_params(P, false, s->streams[0]) == cudaSuccess;
   }
   cudaSetDevice(prev);

@@ -57,6 +57,7 @@ def load_library() -> ctypes.CDLL:
             "sbf_num_words": (U64, [P]),
             "sbf_device_words": (P, [P]),
             "sbf_kernel_variant": (I, [P]),
+            "sbf_device_status": (I, [P, ctypes.POINTER(ctypes.c_uint32), I]),
             "sbf_clear": (I, [P, P]),
             "sbf_get_bits": (I, [P, P]),
             "sbf_copy_bits_device": (I, [P, P, U64, U64, I, P]),
@@ -190,6 +191,14 @@ class SuperBloomFilter:
     def fused(self) -> bool:
         """True if the fused kernels serve this filter (else the generic ones)."""
         return bool(self._lib.sbf_kernel_variant(self._h))
+
+    def device_status(self, clear: bool = False) -> int:
+        """0 while every launch on this filter ran to completion; bit 0 set
+        after a fused query gave up a bounded wait for shard copies (its
+        answers are then incomplete).  Synchronous."""
+        st = ctypes.c_uint32()
+        _check(self._lib.sbf_device_status(self._h, ctypes.byref(st), 1 if clear else 0))
+        return int(st.value)
 
     def device_words_ptr(self) -> int:
         return int(self._lib.sbf_device_words(self._h))

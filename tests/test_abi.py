@@ -90,3 +90,8 @@ def test_layout_argument_checks_without_gpu(lib):
     assert lib.sbf_create_layout(31, 16, 28, 4, 1 << 20, 256, 0, 2, C.byref(h)) == -1
     assert not h.value
     assert lib.sbf_layout(None) == -1
+
+
+def test_device_status_argument_checks_without_gpu(lib):
+    status = ctypes.c_uint32(7)
+    assert lib.sbf_device_status(None, ctypes.byref(status), 0) == -1

@@ -287,6 +287,63 @@ def test_fused_matches_generic_large(params, monkeypatch):
     assert torch.equal(bg, bf) and torch.equal(hg, hf) and torch.equal(sg, sf)
 
 
+@pytest.mark.parametrize("params", [(31, 16, 28, 4, 1 << 33, 512, True),
+                                    (31, 16, 26, 8, 1 << 33, 256, True),
+                                    (31, 20, 26, 4, 1 << 33, 512, True)],
+                         ids=lambda p: "_".join(map(str, p)))
+def test_large_filter_bulk_copies(params):
+    """Filters of 1 GiB load part of their shards with TMA bulk copies on an
+    mbarrier (slots 32..63 of an iteration): words, bits and hits equal the
+    oracle's, and no wait ran out."""
+    g = synth.bacterial_genome(3_000_000, seed=31)
+    goff = np.array([0, g.size], dtype=np.uint64)
+    q, qoff = ragged_reads(60_000, 32, genome=g)
+    f, o = check_insert_query(params, g, goff, q, qoff)
+    assert f.fused and f.nbytes >= 1 << 30
+    assert f.device_status() == 0
+    f.close()
+
+
+def test_batch_mixes_bulk_and_plain_copies():
+    """One persistent launch over a 1 GiB filter (bulk copies) and a 4 MiB
+    one (cp.async only): every warp switches between the two per segment;
+    answers equal the single-filter calls."""
+    from paper_2606_24417_gb300.sbf import BATCH_FUSED, BATCH_GRAPH, FilterBatch
+
+    g = synth.bacterial_genome(2_000_000, seed=33)
+    goff = np.array([0, g.size], dtype=np.uint64)
+    big = make_filter(31, 16, 28, 4, 1 << 33)
+    small = make_filter(31, 16, 28, 4, 1 << 25)
+    for f in (big, small):
+        f.insert(dev(g), dev_off(goff))
+    qa, qa_off = ragged_reads(30_000, 34, genome=g)
+    qb, qb_off = ragged_reads(30_000, 35, genome=g)
+    seq = np.concatenate([qa, qb])
+    off = np.concatenate([qa_off, qa_off[-1] + qb_off[1:]]).astype(np.uint64)
+    group = np.array([0, qa_off.size - 1, off.size - 1], dtype=np.uint64)
+    ref_bits, ref_hits = [], []
+    for f, (qs, qo) in ((big, (qa, qa_off)), (small, (qb, qb_off))):
+        bb, hh = f.query(dev(qs), dev_off(qo))
+        ref_bits.append(u32(bb))
+        ref_hits.append(u32(hh))
+    batch = FilterBatch([big, small])
+    for mode in (BATCH_FUSED, BATCH_GRAPH):
+        for dynamic in (False, True):
+            batch.set_schedule(dynamic, 4)
+            bits, hits = batch.query(dev(seq), dev_off(off), off, group, mode=mode)
+            hb = u32(hits)
+            assert np.array_equal(hb[:qa_off.size - 1], ref_hits[0])
+            assert np.array_equal(hb[qa_off.size - 1:], ref_hits[1])
+            # answer bits of the first group's positions (its reads end where the second begin)
+            na = int(qa_off[-1])
+            gb = u32(bits)
+            assert np.array_equal(gb[:na // 32], ref_bits[0][:na // 32])
+    assert big.device_status() == 0 and small.device_status() == 0
+    batch.close()
+    big.close()
+    small.close()
+
+
 def test_unaligned_sequence_pointer():
     params = (31, 16, 28, 4, 1 << 22, 512, True)
     seq, off = ragged_reads(2000, 51)
