@@ -59,8 +59,12 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 // 2.42 ms, 512 MiB 2.27 -> 2.40 ms; so the switch is at 1 GiB.
 constexpr uint64_t kTmaMinBytes = 1ull << 30;
 constexpr uint32_t kTmaFromSlot = 32;
-// Bound of every wait on that barrier: one second of the global timer.
+// Bound of every wait on that barrier: one second of the global timer.  Each
+// try_wait may suspend the thread for up to kSuspendHintNs instead of
+// returning at once (it resumes when the phase completes), so a waiting warp
+// issues few instructions (queries on a 4 GiB filter 0.5-1% faster).
 constexpr uint64_t kWaitLimitNs = 1000000000ull;
+constexpr uint32_t kSuspendHintNs = 20000;
 
 // Modular inverses of the odd golden-ratio multipliers (Newton iteration).
 __host__ __device__ constexpr uint32_t inv32(uint32_t a) {
@@ -254,9 +258,9 @@ __device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity) {
   while (true) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        : "=r"(done) : "r"(bar), "r"(parity), "n"(kSuspendHintNs) : "memory");
     if (done) return true;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     if (t - t0 > kWaitLimitNs) return false;
