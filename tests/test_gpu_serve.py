@@ -120,3 +120,31 @@ def test_bounded_wait(served):
         hits, _, _ = srv.wait(t, 60)
         assert np.array_equal(hits, _direct(f, seq, off)[1])
     srv.close()
+
+
+def test_large_filter_served_equals_direct():
+    """A 1 GiB filter is served by the bulk-copy query kernels: every request's
+    answers equal a direct query's (checked against the oracle elsewhere) and
+    no wait ran out."""
+    from paper_2606_24417_gb300.sbf import FilterServer, SuperBloomFilter
+
+    g = synth.bacterial_genome(2_000_000, seed=23)
+    f = SuperBloomFilter(31, 16, 28, 4, 1 << 33)
+    f.insert(torch.from_numpy(g).cuda(),
+             torch.from_numpy(np.array([0, g.size], dtype=np.int64)).cuda())
+    reqs = []
+    for i in range(12):
+        n = 50 + 700 * i
+        if i % 2:
+            reqs.append(synth.sample_reads(g, n, 150, 0.01, seed=300 + i))
+        else:
+            reqs.append(synth.random_reads(n, 150, seed=400 + i))
+    srv = FilterServer(f, read_budget_bytes=16 << 20, max_inflight=3)
+    tickets = [srv.submit(seq, off, want_bits=True) for seq, off in reqs]
+    for (seq, off), t in zip(reqs, tickets):
+        hits, bits, _ = srv.wait(t, 60)
+        db, dh = _direct(f, seq, off)
+        assert np.array_equal(hits, dh) and np.array_equal(bits, db)
+    assert f.device_status() == 0
+    srv.close()
+    f.close()

@@ -49,3 +49,38 @@ def test_noalloc_matches_batch_entry_point_twice():
     with pytest.raises(SbfError) as ei:
         batch_query_noalloc(many, dseq, doff, w["off"], group, bits, hits)
     assert ei.value.code == -1 and "at most 512" in str(ei.value)
+
+
+def test_noalloc_with_a_large_filter():
+    """A batch holding a 1 GiB filter takes the bulk-copy kernels; the
+    allocation-free entry point still equals the batch entry point."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_24417_gb300 import build_lib
+
+    build_lib.build()
+    torch.cuda.set_device(0)
+    from paper_2606_24417_gb300.sbf import (BATCH_FUSED, FilterBatch, SuperBloomFilter,
+                                            batch_query_noalloc)
+
+    w = synth.batched_workload(n_filters=3, exp_lo=15, exp_hi=21, genome_lo=200_000,
+                               genome_hi=600_000, n_reads=6000, seed=19, read_cap=20_000)
+    bits_of = [1 << 33] + list(w["bits"][1:])
+    filters = [SuperBloomFilter(31, 16, 28, 4, b) for b in bits_of]
+    batch = FilterBatch(filters)
+    batch.insert(torch.from_numpy(w["gseq"]).cuda(),
+                 torch.from_numpy(w["goff"].astype(np.int64)).cuda(), w["goff"], w["ggroup"],
+                 mode=BATCH_FUSED)
+    dseq = torch.from_numpy(w["seq"]).cuda()
+    doff = torch.from_numpy(w["off"].astype(np.int64)).cuda()
+    want_bits, want_hits = batch.query(dseq, doff, w["off"], w["group"], mode=BATCH_FUSED)
+    bits = torch.full_like(want_bits, -1)
+    hits = torch.full_like(want_hits, -1)
+    batch_query_noalloc(filters, dseq, doff, w["off"], w["group"], bits, hits)
+    torch.cuda.synchronize()
+    assert int(want_hits.sum()) > 0
+    assert torch.equal(bits, want_bits) and torch.equal(hits, want_hits)
+    assert all(f.device_status() == 0 for f in filters)
+    batch.close()
+    for f in filters:
+        f.close()
