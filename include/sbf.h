@@ -78,7 +78,8 @@ enum {
  * (the paper rounds to a power of two; any N is valid here because the shard
  * is chosen by a multiply-high, Sec. IV-B).  Returns SBF_EUNSUPPORTED for a
  * parameter set without a compiled kernel.  The filter owns N * shard_bits / 8
- * bytes of device memory on the current device, zeroed.
+ * bytes of device memory on the current device, zeroed, and a 4-byte status
+ * word (sbf_device_status).
  * ------------------------------------------------------------------------- */
 int sbf_create(int k, int m, int s, int H, uint64_t bits, sbf_filter** out);
 int sbf_create_ex(int k, int m, int s, int H, uint64_t bits, int shard_bits, int canonical,
@@ -185,7 +186,9 @@ int sbf_query_seqs_ex(const sbf_filter* f, const uint8_t* d_seq, uint64_t seq_le
 /* Host-resident input (Sec. V-F): the same operations on host buffers.  The
  * input is copied to the device in chunks on two streams so that copies
  * overlap the kernels; outputs are copied back.  Pinned host memory gives
- * full link speed, pageable memory works.  Synchronous. */
+ * full link speed, pageable memory works.  Synchronous.  A query on a
+ * filter of 1 GiB or more returns SBF_ETIMEOUT if a bounded shard-copy wait
+ * ran out (see sbf_device_status). */
 int sbf_insert_seqs_host(sbf_filter* f, const uint8_t* h_seq, uint64_t seq_len,
                          const uint64_t* h_off, uint64_t n_reads);
 int sbf_query_seqs_host(const sbf_filter* f, const uint8_t* h_seq, uint64_t seq_len,

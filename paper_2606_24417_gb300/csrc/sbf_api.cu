@@ -570,6 +570,14 @@ int host_run_fused(sbf_filter* f, bool is_query, const uint8_t* h_seq, const uin
     if (e != cudaSuccess) return cuda_fail(e, "host path sync");
     copy_out(b);
   }
+  if (is_query && fused::is_big(f->geom)) {  // the bulk-copy kernels' bounded waits
+    uint32_t status = 0;
+    cudaError_t e = cudaMemcpy(&status, f->geom.status, sizeof(status), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (status)
+      return fail(SBF_ETIMEOUT, "a shard-copy wait ran out; answers are incomplete "
+                                "(sbf_device_status reports it until cleared)");
+  }
   if (is_query && h_bits) {
     // word A/32 of a chunk: its bits below off[r0] belong to the previous chunk
     for (size_t ci = 0; ci < chunks.size(); ++ci) {

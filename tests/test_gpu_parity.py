@@ -300,6 +300,10 @@ def test_large_filter_bulk_copies(params):
     q, qoff = ragged_reads(60_000, 32, genome=g)
     f, o = check_insert_query(params, g, goff, q, qoff)
     assert f.fused and f.nbytes >= 1 << 30
+    # the host entry point takes the same kernels and checks the status word itself
+    hb, hh = f.query_host(q, qoff)
+    ob, oh = o.query(q, qoff)
+    assert np.array_equal(hb, ob) and np.array_equal(hh, oh)
     assert f.device_status() == 0
     f.close()
 
