@@ -10,6 +10,9 @@
 //  * Staging: each lane loads 16 raw bytes (one 128-bit non-coherent load),
 //    encodes them ONCE into a 2-bit word (first base most significant), its
 //    reverse complement and a 16-bit invalid-base mask in shared memory.
+//    Consecutive iterations overlap by the words their windows share; those
+//    are carried in shared memory, so every iteration after a range's first
+//    encodes exactly U new words (one per useful lane, no divergent pass).
 //  * Lane chunks: lane l owns positions [16l, 16l+16).  From three staged words
 //    it extracts every m-mer and s-mer by static funnel shifts (no per-k-mer
 //    re-packing, Sec. IV-C / IV-E amortisation taken to the whole chunk).
@@ -433,35 +436,38 @@ __device__ __forceinline__ bool run_range(WarpSmem<H, B, KEY64>& S, const Params
     }
   }
 
-  for (uint64_t it = it0; it < it1; ++it, p0 += ADV) {
-    // ---------------- staging: encode 544 bases once ----------------------
-    {
-      auto stage = [&](int wi, const uint4& raw) {
-        const uint64_t pos = p0 + 16ull * wi;
-        uint32_t c8, b4, fw, bad;
-        encode4(raw.x, c8, b4); fw = c8;             bad = b4;
-        encode4(raw.y, c8, b4); fw = (fw << 8) | c8; bad |= b4 << 4;
-        encode4(raw.z, c8, b4); fw = (fw << 8) | c8; bad |= b4 << 8;
-        encode4(raw.w, c8, b4); fw = (fw << 8) | c8; bad |= b4 << 12;
-        if (pos < lo_pos || pos + 16 > hi_pos) {  // outside the reads' span
-          uint32_t okm = 0;
+  // Staging: encode the 16 bases of word wi at p (bytes raw) once.
+  auto stage = [&](uint64_t p, int wi, const uint4& raw) {
+    const uint64_t pos = p + 16ull * wi;
+    uint32_t c8, b4, fw, bad;
+    encode4(raw.x, c8, b4); fw = c8;             bad = b4;
+    encode4(raw.y, c8, b4); fw = (fw << 8) | c8; bad |= b4 << 4;
+    encode4(raw.z, c8, b4); fw = (fw << 8) | c8; bad |= b4 << 8;
+    encode4(raw.w, c8, b4); fw = (fw << 8) | c8; bad |= b4 << 12;
+    if (pos < lo_pos || pos + 16 > hi_pos) {  // outside the reads' span
+      uint32_t okm = 0;
 #pragma unroll
-          for (int b = 0; b < 16; ++b) okm |= (uint32_t)(pos + b >= lo_pos && pos + b < hi_pos) << b;
-          bad |= ~okm & 0xFFFFu;
-        }
-        S.fwd[wi] = fw;
-        S.rcw[wi] = ~pairswap(__brev(fw));
-        S.bad[wi] = bad;
-      };
-      stage(lane, raw_a);
-      if (lane < kStage - 32) stage(lane + 32, raw_b);
-      // prefetch the next iteration's bytes; they arrive while this one runs
-      if (it + 1 < it1) {
-        const uint64_t np = p0 + ADV;
-        raw_a = load16(seg.seq, np + 16ull * lane, seq_len, aligned);
-        if (lane < kStage - 32) raw_b = load16(seg.seq, np + 16ull * (lane + 32), seq_len, aligned);
-      }
+      for (int b = 0; b < 16; ++b) okm |= (uint32_t)(pos + b >= lo_pos && pos + b < hi_pos) << b;
+      bad |= ~okm & 0xFFFFu;
     }
+    S.fwd[wi] = fw;
+    S.rcw[wi] = ~pairswap(__brev(fw));
+    S.bad[wi] = bad;
+  };
+  // Iterations advance by U*16 bases, so the last NC staged words of one are
+  // the first NC of the next: the range's first iteration stages all kStage
+  // words here, and every iteration stages the next one's other U words at
+  // its end (their bytes prefetched one iteration ahead).
+  constexpr int NC = kStage - U;
+  if (it0 < it1) {
+    stage(p0, lane, raw_a);
+    if (lane < kStage - 32) stage(p0, lane + 32, raw_b);
+    if (it0 + 1 < it1 && lane < U)
+      raw_a = load16(seg.seq, p0 + ADV + 16ull * (lane + NC), seq_len, aligned);
+  }
+
+  for (uint64_t it = it0; it < it1; ++it, p0 += ADV) {
+    // ---------------- staged words of this iteration: into registers ------
     if (lane < 17) {
       S.kill_w[lane] = 0;
       S.own_w[lane] = 0;
@@ -962,6 +968,24 @@ __device__ __forceinline__ bool run_range(WarpSmem<H, B, KEY64>& S, const Params
     }
     r_cur = r_next;
     e_batch = e_next;
+    // ---------------- the next iteration's words ---------------------------
+    if (it + 1 < it1) {
+      uint32_t cf = 0, cr = 0, cb = 0;
+      if (lane < NC) {
+        cf = S.fwd[U + lane];
+        cr = S.rcw[U + lane];
+        cb = S.bad[U + lane];
+      }
+      __syncwarp();
+      if (lane < NC) {
+        S.fwd[lane] = cf;
+        S.rcw[lane] = cr;
+        S.bad[lane] = cb;
+      }
+      if (lane < U) stage(p0 + ADV, lane + NC, raw_a);
+      if (it + 2 < it1 && lane < U)
+        raw_a = load16(seg.seq, p0 + 2 * ADV + 16ull * (lane + NC), seq_len, aligned);
+    }
     __syncwarp();
   }
   return true;
