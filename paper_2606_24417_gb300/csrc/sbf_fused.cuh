@@ -474,7 +474,6 @@ __device__ __forceinline__ bool run_range(WarpSmem<H, B, KEY64>& S, const Params
     }
     __syncwarp();
 
-    const uint64_t Pl = p0 + 16ull * lane;
     const uint32_t F0 = S.fwd[lane], F1 = S.fwd[lane + 1], F2 = S.fwd[lane + 2];
     const uint32_t R0 = S.rcw[lane + 2], R1 = S.rcw[lane + 1], R2 = S.rcw[lane];
     const uint64_t bad48 = (uint64_t)S.bad[lane] | ((uint64_t)S.bad[lane + 1] << 16) |
@@ -485,24 +484,28 @@ __device__ __forceinline__ bool run_range(WarpSmem<H, B, KEY64>& S, const Params
     uint64_t adv = 0;
     const uint64_t own_hi = p0 + ADV;
     {
+      // every read ending in the window marks its last base in position-space
+      // words (pref_w is free until the answers); each lane then reads the
+      // 48 positions from its chunk on
       const uint64_t win_hi = p0 + 16ull * kStage;
+      if (lane < 17) S.pref_w[lane] = 0;
+      __syncwarp();
       uint64_t q0 = r_cur;
       uint64_t e = e_batch;
       while (true) {
         unsigned bw = __ballot_sync(kFull, e < win_hi);
         adv += __popc(__ballot_sync(kFull, e <= own_hi));
-        unsigned bb = bw;
-        while (bb) {
-          int i = __ffs(bb) - 1;
-          bb &= bb - 1;
-          uint64_t ei = __shfl_sync(kFull, e, i);
-          int64_t d = (int64_t)ei - 1 - (int64_t)Pl;   // last base of that read
-          if (d >= 0 && d < 48) E48 |= 1ull << d;
+        if (e < win_hi && e > p0) {
+          const uint32_t d = (uint32_t)(e - 1 - p0);  // last base of that read, < 544
+          atomicOr(&S.pref_w[d >> 5], 1u << (d & 31u));
         }
         if (bw != kFull) break;
         q0 += 32;
         e = read_end(q0 + lane);
       }
+      __syncwarp();
+      const uint64_t w = ((uint64_t)S.pref_w[(lane >> 1) + 1] << 32) | S.pref_w[lane >> 1];
+      E48 = (w >> ((lane & 1) * 16)) & 0xFFFFFFFFFFFFull;
     }
 
     // ---------------- validity of the lane's 16 k-mers --------------------
