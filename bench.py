@@ -771,15 +771,15 @@ def run_sweep(args):
                        "fill": float(np.bitwise_count(words).sum() / (words.size * 64))
                        if hasattr(np, "bitwise_count") else None})
         f.close()
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    with open(os.path.join(ROOT, "gpurun_out", "sweep.json"), "w") as fh:
+    os.makedirs(args.out, exist_ok=True)
+    with open(os.path.join(args.out, "sweep.json"), "w") as fh:
         json.dump(points, fh)
     best = min((p for p in points if p["bits_per_kmer"] == 16), key=lambda p: p["fpr_measured"])
     print(json.dumps({"workload": "sweep: 100 Mbp bacterial-shaped genome, s in {24,26,28,31}, "
                       "m in {12,14,16,20}, H in {1,2,4,8}, shard bits {256,512}, 8/12/16 bits per "
                       "k-mer; 1M sampled + 1M random 150 bp query reads (FPR from the random half)",
                       "points": len(points), "lowest_fpr_at_16_bits": best,
-                      "written": "gpurun_out/sweep.json"}), flush=True)
+                      "written": os.path.join(args.out, "sweep.json")}), flush=True)
     return 0
 
 
@@ -903,8 +903,8 @@ def run_paper_sweep(args):
                 got[f"total_time_{kern}"] = a[kern]["total_ms"] / b[kern]["total_ms"]
                 got[f"insert_time_{kern}"] = a[kern]["insert_ms"] / b[kern]["insert_ms"]
         claims[name] = {"ours": got, "paper": paper}
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    with open(os.path.join(ROOT, "gpurun_out", "paper_sweep.json"), "w") as fh:
+    os.makedirs(args.out, exist_ok=True)
+    with open(os.path.join(args.out, "paper_sweep.json"), "w") as fh:
         json.dump({"points": list(points.values()), "claims": claims,
                    "default_layout": default_layout}, fh)
     print(json.dumps({"workload": "paper sweep: k=31, (s, m, H) axes through (28, 16, 4) and the "
@@ -914,7 +914,7 @@ def run_paper_sweep(args):
                       "(FPR from the random half)",
                       "points": len(points), "claims": claims,
                       "default_layout_same_budget": default_layout,
-                      "written": "gpurun_out/paper_sweep.json"}), flush=True)
+                      "written": os.path.join(args.out, "paper_sweep.json")}), flush=True)
     return 0
 
 
@@ -1172,8 +1172,8 @@ def run_fpr_curve(args):
             rows.append(row)
             log(f"[bench] s={s_} 2^{e}: {fp} false positives")
             f.close()
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    with open(os.path.join(ROOT, "gpurun_out", "fpr_curve.json"), "w") as fh:
+    os.makedirs(args.out, exist_ok=True)
+    with open(os.path.join(args.out, "fpr_curve.json"), "w") as fh:
         json.dump(rows, fh)
     print(json.dumps({"workload": "fpr_curve: 100 Mbp bacterial-shaped genome inserted into "
                       "2^22..2^39-bit filters (k=31, m=16, H=4, 512-bit shards), s in {28,30,31}; "
@@ -1257,8 +1257,8 @@ def run_filter_sizes(args):
         log(f"[bench] 2^{e} bits: query {q_rate / 1e9:.1f} G/s ({q_rate / q_bound:.2f} of bound), "
             f"insert {i_rate / 1e9:.1f} G/s ({i_rate / i_bound:.2f})")
         f.close()
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    with open(os.path.join(ROOT, "gpurun_out", "filter_sizes.json"), "w") as fh:
+    os.makedirs(args.out, exist_ok=True)
+    with open(os.path.join(args.out, "filter_sizes.json"), "w") as fh:
         json.dump(rows, fh)
     print(json.dumps({"workload": "filter_sizes: 100 Mbp bacterial-shaped genome inserted, "
                       f"{n_reads} 150 bp reads queried (half sampled with 1% errors, half random), "
@@ -1280,6 +1280,8 @@ def main():
                     choices=["bacterial", "batched", "served", "sweep", "paper_sweep", "fastx",
                              "alphabets", "fpr_curve", "filter_sizes"],
                     help="batched: the many-filter workload (its own JSON line)")
+    ap.add_argument("--out", default=os.path.join(ROOT, "bench_results"),
+                    help="directory for the per-point JSON of the sweep-type workloads")
     ap.add_argument("--filter-log2", type=int, default=30,
                     help="filter of 2^N bits for the default workload (30: the headline 128 MiB)")
     ap.add_argument("--skip-extras", action="store_true",
