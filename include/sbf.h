@@ -6,8 +6,9 @@
  * picks one shard of shard_bits bits; each of the k-mer's k-s+1 s-mers sets
  * (insert) or tests (query) H bits inside that shard; a query is positive only
  * if every one of those (k-s+1)*H bits is set (Findere, Eq. 2).  Shards are
- * split into min(H, shard_bits/64) sectors and hash i addresses sector
- * i mod S (Sec. IV-B); bit positions come from slices of a 64-bit s-mer hash
+ * split into S sectors, S the largest power of two not above
+ * min(H, shard_bits/64), and hash i addresses sector i mod S (Sec. IV-B; for
+ * H = 3 on 512-bit shards S = 2); bit positions come from slices of a 64-bit s-mer hash
  * (bit-slicing, Sec. IV-G).  The exact hash functions, the canonical-k-mer
  * rule and the 512-bit layout are fixed by this library (see the sbf_create
  * notes below); they are what the parity tests check bit for bit.
@@ -252,10 +253,12 @@ int sbf_batch_tune(sbf_batch* b, int insert, const uint8_t* d_seq, uint64_t seq_
  * device synchronisation.  It answers exactly like sbf_batch_query in
  * SBF_BATCH_FUSED mode (same arguments, the filters passed directly instead of
  * a batch object), but its scratch (a work counter and the per-filter table)
- * lives in a fixed array compiled into the library: 33,024 bytes that every
- * GPU loading the library holds until the process exits.  Hence at most 512
- * filters per call (more: SBF_EINVAL).  No device or pinned memory is
- * allocated; the table is staged through a 4 KB stack buffer.
+ * lives in a fixed array compiled into the library: 45,312 bytes (a 256-byte
+ * header and 512 table entries of 88 bytes) that every GPU loading the
+ * library holds until the process exits.  Hence at most 512 filters per call
+ * (more: SBF_EINVAL).  No device or pinned memory is allocated; the table
+ * reaches the array in the parameters of small kernels (32 entries each), so
+ * the call does not wait on the host for earlier work on its stream.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
  * any stream capture.  All calls on a device share the array and each call
@@ -310,7 +313,10 @@ int sbf_server_stats(sbf_server* s, uint64_t* completed, double* p50_s, double* 
 int sbf_server_reset_stats(sbf_server* s);
 
 /* Number of k-mer start positions sum_r max(0, len_r - k + 1) of a host
- * offset table (valid or not). */
+ * offset table (valid or not): the number of k-mers a batch presents, the
+ * unit of every k-mers/s figure.  It does not size a query output, whose
+ * answer words are indexed by start position in seq (ceil(seq_len / 32)
+ * words, see above); a position where no k-mer starts has a 0 bit. */
 int sbf_num_kmers(const uint64_t* h_off, uint64_t n_reads, int k, uint64_t* out);
 
 /* ---------------------------------------------------------------------------

@@ -72,6 +72,8 @@ def _load():
         lib.oracle_kmer_info.restype = None
         lib.oracle_runs_of_keys.argtypes = [P, P, U64]
         lib.oracle_runs_of_keys.restype = U64
+        lib.oracle_mix64.argtypes = [U64]
+        lib.oracle_mix64.restype = U64
         _lib = lib
     return _lib
 
@@ -190,3 +192,8 @@ def runs_of_keys(keys, active) -> int:
     a = np.ascontiguousarray(np.asarray(active, dtype=np.uint8))
     assert k.size == a.size
     return int(lib.oracle_runs_of_keys(_ptr(k), _ptr(a), k.size))
+
+
+def mix64(x: int) -> int:
+    """The oracle's 64-bit finaliser (SplitMix64's output function)."""
+    return int(_load().oracle_mix64(int(x) & 0xFFFFFFFFFFFFFFFF))

@@ -384,3 +384,5 @@ uint64_t oracle_runs_of_keys(const uint64_t* keys, const uint8_t* active, uint64
   }
   return runs;
 }
+
+uint64_t oracle_mix64(uint64_t x) { return mix64(x); }

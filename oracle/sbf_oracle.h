@@ -78,6 +78,12 @@ void oracle_kmer_info(const oracle_sbf* f, const uint8_t* x, uint64_t* out_minim
  * of consecutive active lanes with equal keys. */
 uint64_t oracle_runs_of_keys(const uint64_t* keys, const uint8_t* active, uint64_t n);
 
+/* The 64-bit finaliser every hash of the filter goes through (the SplitMix64
+ * output function of Steele, Lea and Flood, 2014; Sec. IV-G's "stronger mix
+ * with an additional xorshift").  Exported so that tests can pin it to the
+ * published generator's outputs. */
+uint64_t oracle_mix64(uint64_t x);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,8 +23,29 @@ using sbf::fused::Segment;
 
 constexpr int kMaxFilters = 512;       // largest batch this entry point takes
 constexpr size_t kHeaderBytes = 256;   // work counter, padded to the table's alignment
-constexpr size_t kScratchBytes = kHeaderBytes + kMaxFilters * sizeof(Segment);
-constexpr int kStageSegments = 64;     // host staging buffer on the stack (4 KB)
+static_assert(sizeof(Segment) == 88, "documented scratch size assumes 88-byte segments");
+constexpr size_t kScratchBytes = kHeaderBytes + kMaxFilters * sizeof(Segment);  // 45,312
+static_assert(kScratchBytes == 45312, "documented scratch size");
+// Segments per table-writing launch: they travel by value in the kernel's
+// parameters (32 * 88 = 2,816 bytes, inside the classic 4 KB parameter limit).
+constexpr int kParamSegments = 32;
+
+struct SegmentChunk {
+  Segment seg[kParamSegments];
+};
+
+// Copies `cnt` segments from the kernel parameters to dst[0, cnt), and zeroes
+// the work counter when `work` is not NULL.  The table thus reaches the
+// scratch without a host-to-device copy from pageable memory, which would
+// make the host wait for earlier work on the stream.
+__global__ void write_table_kernel(Segment* dst, SegmentChunk chunk, int cnt,
+                                   unsigned long long* work) {
+  const int words = cnt * (int)(sizeof(Segment) / 8);
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(chunk.seg);
+  uint64_t* out = reinterpret_cast<uint64_t*>(dst);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) out[i] = src[i];
+  if (work && threadIdx.x == 0) *work = 0ull;
+}
 
 // The scratch: a 64-bit work counter at offset 0 and the segment table at
 // kHeaderBytes.  Shared by all calls on a device; each call overwrites it.
@@ -106,13 +127,14 @@ extern "C" int sbf_batch_query_noalloc(sbf_filter* const* filters, int n_filters
   Segment* d_table = reinterpret_cast<Segment*>(scratch + kHeaderBytes);
   cudaError_t e;
 
-  // Segment table, staged through a small stack buffer: a copy from pageable
-  // host memory returns once the data is staged, so the buffer is reusable.
+  // Segment table, written by small kernels that carry it in their parameters
+  // (kParamSegments per launch); the first launch also zeroes the work
+  // counter, which keeps the last call's value otherwise.
   const uint64_t adv = (uint64_t)sbf::fused::advance_of(f0->geom);
-  Segment stage[kStageSegments];
+  SegmentChunk chunk;
   uint64_t iters = 0;
-  for (int c0 = 0; c0 < n_filters; c0 += kStageSegments) {
-    const int cnt = n_filters - c0 < kStageSegments ? n_filters - c0 : kStageSegments;
+  for (int c0 = 0; c0 < n_filters; c0 += kParamSegments) {
+    const int cnt = n_filters - c0 < kParamSegments ? n_filters - c0 : kParamSegments;
     for (int j = 0; j < cnt; ++j) {
       const int fi = c0 + j;
       const uint64_t g0 = h_group[fi], g1 = h_group[fi + 1];
@@ -132,15 +154,11 @@ extern "C" int sbf_batch_query_noalloc(sbf_filter* const* filters, int n_filters
         sg.iters = p_end > sg.p_begin ? (p_end - sg.p_begin + adv - 1) / adv : 0;
       }
       iters += sg.iters;
-      stage[j] = sg;
+      chunk.seg[j] = sg;
     }
-    if ((e = cudaMemcpyAsync(d_table + c0, stage, cnt * sizeof(Segment), cudaMemcpyHostToDevice, st)) !=
-        cudaSuccess)
-      return cuda_fail(e, "segment table copy");
+    write_table_kernel<<<1, 128, 0, st>>>(d_table + c0, chunk, cnt, c0 == 0 ? d_work : nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "segment table write");
   }
-  // The work counter must start at zero: the array keeps the last call's value.
-  if ((e = cudaMemsetAsync(d_work, 0, sizeof(unsigned long long), st)) != cudaSuccess)
-    return cuda_fail(e, "work counter reset");
   if (d_kmer_bits && seq_len &&
       (e = cudaMemsetAsync(d_kmer_bits, 0, ((seq_len + 31) / 32) * 4, st)) != cudaSuccess)
     return cuda_fail(e, "memset");

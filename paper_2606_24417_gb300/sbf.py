@@ -466,6 +466,16 @@ def batch_query_noalloc(filters, seq, off, off_host, group, bits, hits, stream=N
     arr = (ctypes.c_void_p * len(filters))(*[f.handle.value for f in filters])
     oh = np.ascontiguousarray(off_host, dtype=np.uint64)
     gr = np.ascontiguousarray(group, dtype=np.uint64)
+    # the C side reads group[n_filters] and off_host[n_reads] and writes up to
+    # these sizes on the device: refuse short arrays before the call
+    if gr.size != len(filters) + 1:
+        raise SbfError(-1, f"group has {gr.size} entries, want {len(filters) + 1}")
+    if oh.size < 1 or off.numel() != oh.size:
+        raise SbfError(-1, "device and host offsets differ in length")
+    if bits is None or hits is None:
+        raise SbfError(-1, "bits and hits must be preallocated")
+    if bits.numel() < (seq.numel() + 31) // 32 or hits.numel() < oh.size - 1:
+        raise SbfError(-1, "bits or hits too small for the batch")
     _check(lib.sbf_batch_query_noalloc(arr, len(filters), _dev_ptr(seq, 1), seq.numel(),
                                        _dev_ptr(off, 8), _host_ptr(oh), oh.size - 1, _host_ptr(gr),
                                        _dev_ptr(bits, 4), _dev_ptr(hits, 4), _stream_handle(stream)))

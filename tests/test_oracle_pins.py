@@ -37,6 +37,27 @@ def _random_dna(rng, n, alphabet="ACGT"):
 
 
 # ---------------------------------------------------------------------------
+# the 64-bit finaliser: known answers of the published SplitMix64 generator
+# ---------------------------------------------------------------------------
+def test_mix64_matches_published_splitmix64_outputs():
+    """Every hash of the filter (shard choice and s-mer bits, Sec. IV-G) goes
+    through the oracle's mix64, the output function of SplitMix64.  The
+    generator's published first outputs for two seeds pin all five of its
+    steps (three xor-shifts and two multipliers): a transposed constant or
+    a wrong shift changes every output."""
+    from oracle.oracle import mix64
+
+    kat = _golden("splitmix64_kat.json")
+    gamma = int(kat["gamma"], 16)
+    for stream in kat["streams"]:
+        want = stream.get("outputs") or [int(h, 16) for h in stream["outputs_hex"]]
+        state = stream["seed"]
+        for expected in want:
+            state = (state + gamma) & 0xFFFFFFFFFFFFFFFF
+            assert mix64(state) == expected
+
+
+# ---------------------------------------------------------------------------
 # packing and canonical values: closed forms of val = sum c_i 4^(L-1-i)
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("kmer,canonical,expected", [

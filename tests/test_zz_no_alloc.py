@@ -84,3 +84,47 @@ def test_noalloc_with_a_large_filter():
     batch.close()
     for f in filters:
         f.close()
+
+
+def test_noalloc_table_of_many_filters_with_empty_groups():
+    """130 filters (more than one table-writing launch of 32 entries) with a
+    few reads each, so several filters get no reads at all: the table
+    entries after the first launch and their iteration ranges must line up
+    with the batch entry point's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_24417_gb300 import build_lib
+
+    build_lib.build()
+    torch.cuda.set_device(0)
+    from paper_2606_24417_gb300.sbf import (BATCH_FUSED, FilterBatch, SbfError,
+                                            SuperBloomFilter, batch_query_noalloc)
+
+    w = synth.batched_workload(n_filters=130, exp_lo=14, exp_hi=17, genome_lo=5_000,
+                               genome_hi=40_000, n_reads=300, seed=23, read_cap=5_000)
+    sizes = np.diff(w["group"].astype(np.int64))
+    assert (sizes == 0).sum() >= 3 and (sizes > 0).sum() >= 100
+    filters = [SuperBloomFilter(31, 16, 28, 4, b) for b in w["bits"]]
+    batch = FilterBatch(filters)
+    batch.insert(torch.from_numpy(w["gseq"]).cuda(),
+                 torch.from_numpy(w["goff"].astype(np.int64)).cuda(), w["goff"], w["ggroup"],
+                 mode=BATCH_FUSED)
+    dseq = torch.from_numpy(w["seq"]).cuda()
+    doff = torch.from_numpy(w["off"].astype(np.int64)).cuda()
+    want_bits, want_hits = batch.query(dseq, doff, w["off"], w["group"], mode=BATCH_FUSED)
+    torch.cuda.synchronize()
+    assert int(want_hits.sum()) > 0
+    bits = torch.full_like(want_bits, -1)
+    hits = torch.full_like(want_hits, -1)
+    for _ in range(2):
+        batch_query_noalloc(filters, dseq, doff, w["off"], w["group"], bits, hits)
+        torch.cuda.synchronize()
+        assert torch.equal(bits, want_bits) and torch.equal(hits, want_hits)
+    # short output or group arrays are refused before anything reaches the device
+    with pytest.raises(SbfError):
+        batch_query_noalloc(filters, dseq, doff, w["off"], w["group"][:-1], bits, hits)
+    with pytest.raises(SbfError):
+        batch_query_noalloc(filters, dseq, doff, w["off"], w["group"], bits[:1], hits)
+    batch.close()
+    for f in filters:
+        f.close()
