@@ -520,6 +520,25 @@ def run_ours(args, rank, world, local_rank):
     # the oracle baseline is taken on the headline filter only (a 2^34-bit
     # oracle would hold 2 GiB per host process)
     cpu = cpu_baseline(genome, reads, roff) if world == 1 and filter_bits == FILTER_BITS else None
+    # the same workload on filters far beyond the 129 MB L2 (1 GiB and 4 GiB),
+    # each against the random-sector roofline of a buffer of its own size
+    sizes = None
+    if world == 1 and filter_bits == FILTER_BITS:
+        del f
+        sizes = {}
+        for e in (33, 35):
+            row = measure_filter_size(e, args.steps, dev, stream, genome, reads, roff, d_genome,
+                                      d_goff, d_reads, d_roff, d_bits, d_hits, flush)
+            sizes[f"2^{e}"] = {k: row[k] for k in (
+                "filter_bytes", "insert_kmers_per_s", "query_kmers_per_s", "insert_ms", "query_ms",
+                "insert_frac", "query_frac", "probe_gather_gbs", "probe_rmw_gbs",
+                "device_status")}
+            log(f"[bench] 2^{e} bits: query {row['query_kmers_per_s'] / 1e9:.1f} G/s "
+                f"({row['query_frac']:.3f} of its sector bound), insert "
+                f"{row['insert_kmers_per_s'] / 1e9:.1f} G/s ({row['insert_frac']:.3f})")
+        sizes["note"] = ("median of max(steps, 3) steps per size; frac = k-mers/s over streamed "
+                         "bytes at the copy peak plus one shard per super-k-mer run at the "
+                         "random-sector probe's rate over a buffer of the filter's size")
     line = {
         "metric": METRIC, "value": value, "unit": "k-mers/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -542,6 +561,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "filter_sizes": sizes,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -1182,6 +1202,67 @@ def run_fpr_curve(args):
     return 0
 
 
+def measure_filter_size(e, steps, dev, stream, genome, reads, roff, d_genome, d_goff, d_reads,
+                        d_roff, d_bits, d_hits, flush):
+    """One filter size of the bacterial workload: median insert and query
+    times over max(steps, 3) steps after 3 warm-up steps (L2 flushed before
+    each), each set against the random-sector roofline of a buffer of the
+    filter's size (streamed bytes at the copy peak plus one shard per
+    super-k-mer run at the probe's rate; read-modify-write for the insert)."""
+    import torch
+
+    from paper_2606_24417_gb300.sbf import SuperBloomFilter
+
+    peak, _ = measured_peaks()
+    sector_b = SHARD_BITS // 8
+    n_reads = roff.size - 1
+    ins_kmers = genome.size - K + 1
+    q_kmers = n_reads * (READ_LEN - K + 1)
+    stats = torch.zeros(3, dtype=torch.int64, device=dev)
+    f = SuperBloomFilter(K, M, S, H, 1 << e, shard_bits=SHARD_BITS)
+    # runs (one shard each) of the query and of the insert
+    f.insert(d_genome, d_goff)
+    f.query(d_reads, d_roff, bits=d_bits, hits=d_hits, stats=stats)
+    torch.cuda.synchronize()
+    runs_q = int(stats[1].item())
+    stats.zero_()
+    f.query(d_genome, d_goff, want_bits=False, want_hits=False, stats=stats)
+    torch.cuda.synchronize()
+    runs_i = int(stats[1].item())
+    t_i, t_q = [], []
+    for rep in range(3 + max(steps, 3)):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        flush.fill_(1)
+        f.clear()
+        ev[0].record(stream)
+        f.insert(d_genome, d_goff)
+        ev[1].record(stream)
+        f.query(d_reads, d_roff, bits=d_bits, hits=d_hits)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        if rep >= 3:
+            t_i.append(ev[0].elapsed_time(ev[1]))
+            t_q.append(ev[1].elapsed_time(ev[2]))
+    ins_ms, q_ms = statistics.median(t_i), statistics.median(t_q)
+    fbytes = f.nbytes
+    status = f.device_status()
+    g_gbs = sector_bandwidth(dev, stream, fbytes, sector_b, False, 1 << 27)
+    r_gbs = sector_bandwidth(dev, stream, fbytes, sector_b, True, 1 << 25)
+    q_stream = reads.nbytes + roff.nbytes + (reads.size + 7) // 8 + 4 * n_reads
+    q_bound = q_kmers / (q_stream / (peak * 1e9) + runs_q * sector_b / (g_gbs * 1e9))
+    i_bound = ins_kmers / (genome.nbytes / (peak * 1e9) + runs_i * 2 * sector_b / (r_gbs * 1e9))
+    q_rate, i_rate = q_kmers / (q_ms / 1e3), ins_kmers / (ins_ms / 1e3)
+    row = {"log2_bits": e, "filter_bytes": fbytes, "in_l2": fbytes <= (96 << 20),
+           "insert_ms": ins_ms, "query_ms": q_ms,
+           "insert_kmers_per_s": i_rate, "query_kmers_per_s": q_rate,
+           "probe_gather_gbs": g_gbs, "probe_rmw_gbs": r_gbs,
+           "query_sector_bound": q_bound, "insert_sector_bound": i_bound,
+           "query_frac": q_rate / q_bound, "insert_frac": i_rate / i_bound,
+           "positive_kmers": int(d_hits.sum().item()), "device_status": status}
+    f.close()
+    return row
+
+
 def run_filter_sizes(args):
     """The bacterial workload (100 Mbp genome inserted, 20M 150 bp reads
     queried; k=31, m=16, s=28, H=4, 512-bit shards) on filters of 8 MiB to
@@ -1192,7 +1273,6 @@ def run_filter_sizes(args):
     import torch
 
     from paper_2606_24417_gb300 import build_lib
-    from paper_2606_24417_gb300.sbf import SuperBloomFilter
 
     build_lib.build()
     torch.cuda.set_device(0)
@@ -1200,63 +1280,22 @@ def run_filter_sizes(args):
     stream = torch.cuda.current_stream()
     genome, reads, roff = make_workload(0, small=args.case == "small")
     n_reads = roff.size - 1
-    ins_kmers = genome.size - K + 1
-    q_kmers = n_reads * (READ_LEN - K + 1)
     d_genome = torch.from_numpy(genome).to(dev)
     d_goff = torch.tensor([0, genome.size], dtype=torch.int64, device=dev)
     d_reads = torch.from_numpy(reads).to(dev)
     d_roff = torch.from_numpy(roff.astype(np.int64)).to(dev)
     d_bits = torch.empty((reads.size + 31) // 32, dtype=torch.int32, device=dev)
     d_hits = torch.empty(n_reads, dtype=torch.int32, device=dev)
-    stats = torch.zeros(3, dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     peak, peak_kind = measured_peaks()
-    sector_b = SHARD_BITS // 8
     rows = []
     for e in (26, 27, 28, 29, 30, 31, 32, 33, 35):
-        f = SuperBloomFilter(K, M, S, H, 1 << e, shard_bits=SHARD_BITS)
-        # runs (one shard each) of the query and of the insert
-        stats.zero_()
-        f.insert(d_genome, d_goff)
-        f.query(d_reads, d_roff, bits=d_bits, hits=d_hits, stats=stats)
-        torch.cuda.synchronize()
-        runs_q = int(stats[1].item())
-        stats.zero_()
-        f.query(d_genome, d_goff, want_bits=False, want_hits=False, stats=stats)
-        torch.cuda.synchronize()
-        runs_i = int(stats[1].item())
-        t_i, t_q = [], []
-        for rep in range(3 + max(args.steps, 3)):
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            flush.fill_(1)
-            f.clear()
-            ev[0].record(stream)
-            f.insert(d_genome, d_goff)
-            ev[1].record(stream)
-            f.query(d_reads, d_roff, bits=d_bits, hits=d_hits)
-            ev[2].record(stream)
-            torch.cuda.synchronize()
-            if rep >= 3:
-                t_i.append(ev[0].elapsed_time(ev[1]))
-                t_q.append(ev[1].elapsed_time(ev[2]))
-        ins_ms, q_ms = statistics.median(t_i), statistics.median(t_q)
-        fbytes = f.nbytes
-        g_gbs = sector_bandwidth(dev, stream, fbytes, sector_b, False, 1 << 27)
-        r_gbs = sector_bandwidth(dev, stream, fbytes, sector_b, True, 1 << 25)
-        q_stream = reads.nbytes + roff.nbytes + (reads.size + 7) // 8 + 4 * n_reads
-        q_bound = q_kmers / (q_stream / (peak * 1e9) + runs_q * sector_b / (g_gbs * 1e9))
-        i_bound = ins_kmers / (genome.nbytes / (peak * 1e9) + runs_i * 2 * sector_b / (r_gbs * 1e9))
-        q_rate, i_rate = q_kmers / (q_ms / 1e3), ins_kmers / (ins_ms / 1e3)
-        rows.append({"log2_bits": e, "filter_bytes": fbytes, "in_l2": fbytes <= (96 << 20),
-                     "insert_ms": ins_ms, "query_ms": q_ms,
-                     "insert_kmers_per_s": i_rate, "query_kmers_per_s": q_rate,
-                     "probe_gather_gbs": g_gbs, "probe_rmw_gbs": r_gbs,
-                     "query_sector_bound": q_bound, "insert_sector_bound": i_bound,
-                     "query_frac": q_rate / q_bound, "insert_frac": i_rate / i_bound,
-                     "positive_kmers": int(d_hits.sum().item())})
-        log(f"[bench] 2^{e} bits: query {q_rate / 1e9:.1f} G/s ({q_rate / q_bound:.2f} of bound), "
-            f"insert {i_rate / 1e9:.1f} G/s ({i_rate / i_bound:.2f})")
-        f.close()
+        row = measure_filter_size(e, args.steps, dev, stream, genome, reads, roff, d_genome,
+                                  d_goff, d_reads, d_roff, d_bits, d_hits, flush)
+        rows.append(row)
+        log(f"[bench] 2^{e} bits: query {row['query_kmers_per_s'] / 1e9:.1f} G/s "
+            f"({row['query_frac']:.2f} of bound), insert {row['insert_kmers_per_s'] / 1e9:.1f} G/s "
+            f"({row['insert_frac']:.2f})")
     os.makedirs(args.out, exist_ok=True)
     with open(os.path.join(args.out, "filter_sizes.json"), "w") as fh:
         json.dump(rows, fh)

@@ -134,6 +134,13 @@ class OracleSBF:
         buf = (ctypes.c_uint64 * self.n_words).from_address(addr)
         return np.frombuffer(buf, dtype=np.uint64).copy()
 
+    def words_view(self) -> np.ndarray:
+        """The filter's uint64 words without a copy; valid while this object
+        lives (for tests that reduce multi-GiB filters across processes)."""
+        addr = self._lib.oracle_words(self._h)
+        buf = (ctypes.c_uint64 * self.n_words).from_address(addr)
+        return np.frombuffer(buf, dtype=np.uint64)
+
     def set_words(self, w: np.ndarray) -> None:
         w = _u64(w)
         assert w.size == self.n_words

@@ -441,11 +441,12 @@ def batched_workload(n_filters: int = 256, exp_lo: int = 20, exp_hi: int = 28,
     order = np.argsort(owner, kind="stable")
     owner, lens, sampled = owner[order], lens[order], sampled[order]
     group = np.searchsorted(owner, np.arange(n_filters + 1)).astype(np.uint64)
-    parts = []
-    for f in range(n_filters):
+    parts = [None] * n_filters
+
+    def reads_of(f):
         a, b = int(group[f]), int(group[f + 1])
         if a == b:
-            continue
+            return
         L, smp = lens[a:b], sampled[a:b]
         piece_s = sample_variable_reads(genomes[f], L[smp], 0.01, seed + 11 * f + 1)
         piece_r = uniform_dna(int(L[~smp].sum()), seed * 7919 + f)
@@ -453,19 +454,16 @@ def batched_workload(n_filters: int = 256, exp_lo: int = 20, exp_hi: int = 28,
         Lc = np.minimum(L, np.where(smp, genomes[f].size, L))
         cum_s = np.concatenate([[0], np.cumsum(Lc[smp])])
         cum_r = np.concatenate([[0], np.cumsum(L[~smp])])
-        out = np.empty(int(Lc.sum()), dtype=np.uint8)
-        pos = 0
-        si = ri = 0
-        for is_s, l in zip(smp, Lc):
-            if is_s:
-                out[pos:pos + l] = piece_s[cum_s[si]:cum_s[si + 1]]
-                si += 1
-            else:
-                out[pos:pos + l] = piece_r[cum_r[ri]:cum_r[ri + 1]]
-                ri += 1
-            pos += l
+        src = np.empty(L.size, dtype=np.int64)     # start of each read in piece_s ++ piece_r
+        src[smp] = cum_s[:-1]
+        src[~smp] = piece_s.size + cum_r[:-1]
+        dst = np.concatenate([[0], np.cumsum(Lc)])
+        idx = np.repeat(src - dst[:-1], Lc) + np.arange(int(dst[-1]), dtype=np.int64)
+        parts[f] = np.concatenate([piece_s, piece_r])[idx]
         lens[a:b] = Lc
-        parts.append(out)
+
+    _parallel(reads_of, range(n_filters))
+    parts = [p for p in parts if p is not None]
     seq = np.concatenate(parts) if parts else np.zeros(0, np.uint8)
     off = np.zeros(n_reads + 1, dtype=np.uint64)
     np.cumsum(lens, out=off[1:])
