@@ -162,6 +162,18 @@ int sbf_set_bits(sbf_filter* f, const uint64_t* h_words);
 int sbf_copy_bits_device(sbf_filter* f, uint64_t* d_words, uint64_t word_begin, uint64_t n_words,
                          int to_filter, sbf_stream_t stream);
 
+/* Word-wise OR of n_parts device arrays of n_words uint64 words each, laid
+ * out back to back in d_in (piece j at d_in + j * n_words):
+ * d_out[i] = OR over j of d_in[j * n_words + i].  Filters that inserted
+ * disjoint read shares combine this way (Alg. 1: a filter is the OR of the
+ * bits its k-mers set); the multi-process insert runs it on each rank's
+ * slice of the words after an all-to-all exchange.  Both pointers are
+ * caller-owned device memory, 16-byte aligned, and must not overlap; n_words
+ * must be even when n_parts > 1 (every piece 16-byte aligned).  Asynchronous
+ * on `stream`; SBF_EINVAL for a NULL pointer, misalignment or n_parts < 1. */
+int sbf_or_reduce_device(uint64_t* d_out, const uint64_t* d_in, uint64_t n_words, int n_parts,
+                         sbf_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Insert and query (Alg. 1 and Alg. 2).  Device pointers.
  *

@@ -61,6 +61,7 @@ def load_library() -> ctypes.CDLL:
             "sbf_clear": (I, [P, P]),
             "sbf_get_bits": (I, [P, P]),
             "sbf_copy_bits_device": (I, [P, P, U64, U64, I, P]),
+            "sbf_or_reduce_device": (I, [P, P, U64, I, P]),
             "sbf_set_bits": (I, [P, P]),
             "sbf_insert_seqs": (I, [P, P, U64, P, U64, P]),
             "sbf_query_seqs": (I, [P, P, U64, P, U64, U32P, U32P, P]),
@@ -456,6 +457,16 @@ class FilterServer:
 
     def reset_stats(self) -> None:
         _check(self._lib.sbf_server_reset_stats(self._h))
+
+
+def or_reduce_device(out, parts, stream=None) -> None:
+    """out[i] = OR over rows j of parts[j, i]: int64 CUDA tensors, parts of
+    shape (n_parts, n) contiguous, out of n elements (the OR of filters that
+    inserted disjoint read shares).  Asynchronous on `stream`."""
+    if parts.dim() != 2 or not parts.is_contiguous() or out.numel() != parts.shape[1]:
+        raise SbfError(-1, "parts must be a contiguous (n_parts, n) tensor and out hold n words")
+    _check(load_library().sbf_or_reduce_device(_dev_ptr(out, 8), _dev_ptr(parts, 8), out.numel(),
+                                               parts.shape[0], _stream_handle(stream)))
 
 
 def batch_query_noalloc(filters, seq, off, off_host, group, bits, hits, stream=None):

@@ -75,3 +75,30 @@ def test_read_shares_cover_all_reads():
         shares = [read_share(off, r, world) for r in range(world)]
         assert shares[0][0] == 0 and shares[-1][1] == off.size - 1
         assert all(shares[i][1] == shares[i + 1][0] for i in range(world - 1))
+
+
+@pytest.mark.parametrize("n_parts,n", [(1, 1), (1, 1001), (3, 1000), (8, 1 << 20), (2, 2)])
+def test_or_reduce_kernel(n_parts, n):
+    """The device OR of the multi-GPU insert: out[i] = OR of parts[j, i],
+    against torch's OR of the same rows (odd lengths with one part, even
+    lengths with several: every piece stays 16-byte aligned)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_24417_gb300 import build_lib
+
+    build_lib.build()
+    from paper_2606_24417_gb300.sbf import SbfError, or_reduce_device
+
+    g = torch.Generator(device="cpu").manual_seed(n_parts * 1000 + n)
+    a = torch.randint(-(1 << 62), 1 << 62, (n_parts, n), generator=g, dtype=torch.int64)
+    a &= torch.randint(-(1 << 62), 1 << 62, (n_parts, n), generator=g, dtype=torch.int64)
+    parts = a.cuda()
+    out = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+    or_reduce_device(out, parts)
+    want = a[0].clone()
+    for r in range(1, n_parts):
+        want |= a[r]
+    assert torch.equal(out.cpu(), want)
+    if n_parts == 3:
+        with pytest.raises(SbfError):      # pieces of an odd length would be misaligned
+            or_reduce_device(out[:999], parts[:, :999].contiguous())
