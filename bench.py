@@ -539,6 +539,16 @@ def run_ours(args, rank, world, local_rank):
         sizes["note"] = ("median of max(steps, 3) steps per size; frac = k-mers/s over streamed "
                          "bytes at the copy peak plus one shard per super-k-mer run at the "
                          "random-sector probe's rate over a buffer of the filter's size")
+    # the served workload (its own genome, filter and request pool), so that
+    # the line carries served throughput and p50 / p99 latency
+    served = None
+    if world == 1 and filter_bits == FILTER_BITS and not args.no_served:
+        del d_genome, d_reads, d_bits, d_hits
+        torch.cuda.empty_cache()
+        served = served_measurement(n_poisson=400)
+        served["note"] = ("3.1 Gbp human-shaped genome in a 2^35-bit filter; 200 requests of "
+                          "1 kb-10 Mbp of 150 bp reads (1% errors) in pinned host memory; "
+                          "backlogs of 400 requests, 400 Poisson arrivals per load")
     line = {
         "metric": METRIC, "value": value, "unit": "k-mers/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -562,6 +572,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "cpu_baseline": cpu,
         "filter_sizes": sizes,
+        "served": served,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -619,6 +630,23 @@ def run_batched(args):
         answers[name] = (bits.clone(), hits.clone())
     same = all(torch.equal(answers[n][0], answers["per_filter"][0]) and
                torch.equal(answers[n][1], answers["per_filter"][1]) for n in answers)
+    # a small batch (every 500th read, 10,000 reads over the same 256 filters),
+    # where launch overhead is a visible part of the call: per-filter
+    # launches, one fused launch, and the fused launch replayed from a graph
+    sel = np.arange(0, w["off"].size - 1, 500)
+    owner = np.searchsorted(w["group"].astype(np.int64), sel, side="right") - 1
+    s_len = np.diff(w["off"].astype(np.int64))[sel]
+    s_seq = np.concatenate([w["seq"][int(w["off"][r]):int(w["off"][r + 1])] for r in sel])
+    s_off = np.concatenate([[0], np.cumsum(s_len)]).astype(np.uint64)
+    s_group = np.searchsorted(owner, np.arange(len(filters) + 1)).astype(np.uint64)
+    dsq = torch.from_numpy(s_seq).cuda()
+    dso = torch.from_numpy(s_off.astype(np.int64)).cuda()
+    sb = torch.empty((s_seq.size + 31) // 32, dtype=torch.int32, device="cuda")
+    sh = torch.empty(sel.size, dtype=torch.int32, device="cuda")
+    small = {"reads": int(sel.size), "kmers": num_kmers(s_off, K)}
+    for name, mode in [("per_filter", BATCH_PER_FILTER), ("fused", BATCH_FUSED), ("graph", BATCH_GRAPH)]:
+        small[f"query_ms_{name}"] = timed(
+            lambda: batch.query(dsq, dso, s_off, s_group, bits=sb, hits=sh, mode=mode), 50)
     dyn, chunk, grid = batch.schedule()
     idyn, ichunk, igrid = batch.schedule(insert=True)
     line = {"workload": "batched: 256 filters of 2^20-2^28 bits (log-uniform sizes) built from "
@@ -634,7 +662,8 @@ def run_batched(args):
                                          "tuned_ms": tuned_ms},
                                "insert": {"dynamic": idyn, "chunk": ichunk, "grid_blocks": igrid,
                                           "tuned_ms": tuned_ins_ms}},
-            "answers_identical_across_modes": same}
+            "answers_identical_across_modes": same,
+            "small_batch": small}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -642,17 +671,25 @@ def run_batched(args):
 # ---------------------------------------------------------------------------
 # served workload: resident 4 GiB filter, Poisson requests, p50/p99
 # ---------------------------------------------------------------------------
-def run_served(args):
+def served_measurement(n_poisson: int = 1000):
+    """The served workload: the 3.1 Gbp human-shaped genome in a 2^35-bit
+    (4 GiB) filter resident in HBM; a pool of 200 requests of log-uniform
+    1 kb-10 Mbp of 150 bp reads with 1% errors in pinned host memory.
+    Measures, on the same requests: the kernel's rate when all of them are
+    device-resident in one launch (the direct-query rate) and in one launch
+    each; the server's backlog rate with one client submitting all requests
+    in one call, one client submitting one call per request and four
+    clients; one launch per request through the server; and Poisson arrivals
+    at 0.5 / 0.8 / 0.95 of the one-client backlog rate (p50 / p99 latency,
+    with the time per stage).  Returns a dict."""
     import torch
 
-    from paper_2606_24417_gb300 import build_lib, synth
+    from paper_2606_24417_gb300 import synth
     from paper_2606_24417_gb300.sbf import FilterServer, SuperBloomFilter
 
-    build_lib.build()
-    torch.cuda.set_device(0)
     t = time.time()
     genome = synth.human_like_genome(3_100_000_000, seed=5)
-    log(f"[bench] human-shaped genome generated in {time.time() - t:.1f}s (GC {synth.gc_fraction(genome[:10**8]):.3f})")
+    log(f"[bench] human-shaped genome generated in {time.time() - t:.1f}s")
     f = SuperBloomFilter(K, M, S, H, 1 << 35, shard_bits=SHARD_BITS)
     dg = torch.from_numpy(genome).cuda()
     do = torch.from_numpy(np.array([0, genome.size], dtype=np.int64)).cuda()
@@ -665,7 +702,6 @@ def run_served(args):
     torch.cuda.synchronize()
     insert_ms = e0.elapsed_time(e1)
     del dg
-    # request pool: 1 kb - 10 Mbp of 150 bp reads with 1% errors (log-uniform sizes)
     n_pool = 200
     sizes = np.exp(np.log(1e3) + synth.uniform01(9, 1, 0, n_pool) * (np.log(1e7) - np.log(1e3)))
     pool = []
@@ -675,20 +711,51 @@ def run_served(args):
         pool.append((torch.from_numpy(seq).pin_memory().numpy(),
                      torch.from_numpy(off.view(np.int64)).pin_memory().numpy().view(np.uint64),
                      n * (READ_LEN - K + 1)))
-    mean_kmers = float(np.mean([p[2] for p in pool]))
+    del genome
+    pool_kmers = float(sum(p[2] for p in pool))
+    mean_kmers = pool_kmers / n_pool
     log(f"[bench] {n_pool} requests, {sum(p[0].size for p in pool) / 1e6:.0f} Mbp, "
         f"mean {mean_kmers / 1e3:.0f}k k-mers")
 
-    def backlog(srv, reps=2, clients=1):
-        """Every pool request `reps` times, submitted by `clients` threads at
-        once (ctypes releases the GIL during each submit), then waited for."""
+    # the direct-query rate on the same requests, device-resident
+    allseq = np.concatenate([p[0] for p in pool])
+    alloff = np.concatenate([[0], np.cumsum([p[0].size for p in pool])])
+    lens = np.concatenate([np.diff(p[1].astype(np.int64)) for p in pool])
+    reads_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    d_all, d_alloff = torch.from_numpy(allseq).cuda(), torch.from_numpy(reads_off).cuda()
+    d_reqs = [(d_all[int(alloff[i]):int(alloff[i + 1])],
+               torch.from_numpy(p[1].view(np.int64)).cuda()) for i, p in enumerate(pool)]
+    hits_all = torch.empty(reads_off.size - 1, dtype=torch.int32, device="cuda")
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps / 1e3
+
+    one_launch_s = timed(lambda: f.query(d_all, d_alloff, want_bits=False, hits=hits_all))
+    per_req_s = timed(lambda: [f.query(s_, o_, want_bits=False) for s_, o_ in d_reqs], reps=1)
+    del d_all, d_reqs
+
+    def backlog(srv, clients=1, batch=False, reps=2):
+        """Every pool request `reps` times from `clients` threads, then waited for."""
         srv.reset_stats()
-        work = [p for _ in range(reps) for p in pool]
+        work = [(p[0], p[1]) for _ in range(reps) for p in pool]
         tickets = [None] * len(work)
 
         def client(c):
-            for i in range(c, len(work), clients):
-                tickets[i] = srv.submit(work[i][0], work[i][1])
+            idx = list(range(c, len(work), clients))
+            if batch:
+                for i, tk in zip(idx, srv.submit_many([work[i] for i in idx])):
+                    tickets[i] = tk
+            else:
+                for i in idx:
+                    tickets[i] = srv.submit(*work[i])
 
         ths = [threading.Thread(target=client, args=(c,)) for c in range(clients)]
         for th in ths:
@@ -698,28 +765,30 @@ def run_served(args):
         for tk in tickets:
             srv.wait(tk, 600)
         st = srv.stats()
-        st["clients"] = clients
+        st.update(clients=clients, one_call=batch, breakdown=srv.breakdown())
         return st
 
-    out = {}
+    out = {"insert_ms": insert_ms,
+           "direct": {"one_launch_kmers_per_s": pool_kmers / one_launch_s,
+                      "launch_per_request_kmers_per_s": pool_kmers / per_req_s}}
     srv = FilterServer(f, read_budget_bytes=1 << 30, max_inflight=3)
-    backlog(srv, 1)  # warm
-    peak = backlog(srv)
-    out["peak"] = peak
-    out["peak_4_clients"] = backlog(srv, clients=4)
+    backlog(srv, batch=True, reps=1)  # warm
+    out["backlog_1_client_one_call"] = backlog(srv, batch=True)
+    out["backlog_1_client"] = backlog(srv)
+    out["backlog_4_clients"] = backlog(srv, clients=4)
     one = FilterServer(f, read_budget_bytes=1 << 30, max_inflight=3, max_per_launch=1)
-    backlog(one, 1)
+    backlog(one, reps=1)
     out["one_launch_per_request"] = backlog(one)
     one.close()
+    peak = out["backlog_1_client"]["kmers_per_s"]
     loads = {}
     for load in (0.5, 0.8, 0.95):
-        rate = load * peak["kmers_per_s"] / mean_kmers  # requests per second
-        n_sub = 1000
-        arrivals = synth.poisson_arrivals(n_sub, rate, seed=int(load * 100))
+        rate = load * peak / mean_kmers  # requests per second
+        arrivals = synth.poisson_arrivals(n_poisson, rate, seed=int(load * 100))
         srv.reset_stats()
         tickets = []
         t0 = time.perf_counter()
-        for i in range(n_sub):
+        for i in range(n_poisson):
             while time.perf_counter() - t0 < arrivals[i]:
                 pass
             p = pool[i % n_pool]
@@ -727,16 +796,33 @@ def run_served(args):
         for tk in tickets:
             srv.wait(tk, 600)
         st = srv.stats()
-        st["offered_load"] = load
-        st["offered_requests_per_s"] = rate
-        st["achieved_requests_per_s"] = n_sub / (time.perf_counter() - t0)
+        st.update(offered_load=load, offered_requests_per_s=rate,
+                  achieved_requests_per_s=n_poisson / (time.perf_counter() - t0),
+                  breakdown=srv.breakdown())
         loads[str(load)] = st
     out["poisson"] = loads
     srv.close()
+    f.close()
+    direct = out["direct"]["one_launch_kmers_per_s"]
+    out["served_over_direct"] = {k: out[k]["kmers_per_s"] / direct for k in
+                                 ("backlog_1_client_one_call", "backlog_1_client",
+                                  "backlog_4_clients", "one_launch_per_request")}
+    out["p99_over_p50"] = {k: v["p99_s"] / v["p50_s"] if v["p50_s"] else None
+                           for k, v in loads.items()}
+    return out
+
+
+def run_served(args):
+    import torch
+
+    from paper_2606_24417_gb300 import build_lib
+
+    build_lib.build()
+    torch.cuda.set_device(0)
+    out = served_measurement()
     line = {"workload": "served: 3.1 Gbp order-5 Markov genome (GC 41%, 45% interspersed repeat copies "
                         "of 500 families 300 bp-6 kb, 10% divergence) in a 2^35-bit filter resident in "
                         "HBM; requests of 1 kb-10 Mbp of 150 bp reads with 1% errors, Poisson arrivals",
-            "insert_ms": insert_ms, "insert_kmers_per_s": (genome.size - K + 1) / (insert_ms / 1e3),
             **out}
     print(json.dumps(line), flush=True)
     return 0
@@ -1323,6 +1409,8 @@ def main():
                     help="directory for the per-point JSON of the sweep-type workloads")
     ap.add_argument("--filter-log2", type=int, default=30,
                     help="filter of 2^N bits for the default workload (30: the headline 128 MiB)")
+    ap.add_argument("--no-served", action="store_true",
+                    help="leave the served workload out of the default line")
     ap.add_argument("--skip-extras", action="store_true",
                     help="device-timed steps only (no e2e, no CPU baseline): profiling runs")
     args = ap.parse_args()

@@ -248,11 +248,12 @@ int sbf_batch_set_schedule(sbf_batch* b, int insert, int dynamic, uint32_t chunk
                            uint32_t grid_blocks);
 int sbf_batch_get_schedule(const sbf_batch* b, int insert, int* dynamic, uint32_t* chunk,
                            uint32_t* grid_blocks);
-/* Autotuner: times every candidate schedule (static split; dynamic chunks of
- * 4 to 1024 iterations) on this exact call (insert != 0: the insert) with
- * CUDA events, keeps the fastest for that operation and returns its time in
- * *best_ms.  Synchronises; the call's outputs are left as a normal call
- * leaves them. */
+/* Autotuner: times candidate schedules on this exact call (insert != 0: the
+ * insert) with CUDA events -- first the static split and dynamic chunks of 4
+ * to 1024 iterations at full occupancy, then the best of those with the grid
+ * capped at 1, 2 and 3 blocks per SM -- keeps the fastest for that operation
+ * and returns its time in *best_ms.  Synchronises; the call's outputs are
+ * left as a normal call leaves them. */
 int sbf_batch_tune(sbf_batch* b, int insert, const uint8_t* d_seq, uint64_t seq_len,
                    const uint64_t* d_off, const uint64_t* h_off, uint64_t n_reads,
                    const uint64_t* h_group, uint32_t* d_kmer_bits, uint32_t* d_read_hits,
@@ -286,42 +287,72 @@ int sbf_batch_query_noalloc(sbf_filter* const* filters, int n_filters, const uin
  * Not in the paper.
  *
  * sbf_server_create: the filter (with a fused kernel) stays resident; the
- *   server owns read_budget_bytes of device memory for request reads (plus
- *   three eighths of that for offsets, hit counts and answer words), pinned
- *   host memory of three eighths of it where results land before they are
- *   copied to the caller's buffers (so result buffers may be pageable), and
- *   a worker thread.  Queued
- *   requests are admitted while that memory has room, every request admitted
- *   at one moment (at most max_per_launch of them, 1..65536) is served by ONE
- *   kernel launch (one segment each), and up to max_inflight (1..16)
- *   launches run at once on separate streams, so requests that arrive while
- *   others run overlap with them.  max_per_launch = 1 gives one launch per
- *   request, the baseline continuous batching is measured against.
+ *   server takes read_budget_bytes as its budget of request reads in flight
+ *   and owns device memory for it (a read arena of that size, offsets and
+ *   results of a quarter and three eighths of it), a pinned mirror of the
+ *   result memory where results land before they are copied to the callers'
+ *   buffers (so result buffers may be pageable), and a worker thread.
+ *   Queued requests are admitted while that memory and budget have room,
+ *   every request admitted at one moment (at most max_per_launch of them,
+ *   1..65536) is served by ONE kernel launch (one segment each), and up to
+ *   max_inflight (1..16) launches run at once on separate streams, so
+ *   requests that arrive while others run overlap with them.  A launch takes
+ *   no further request once its reads reach read_budget_bytes /
+ *   (max_inflight + 1), so a deep queue becomes several launches whose
+ *   result copies overlap the next one's kernel.
+ *   max_per_launch = 1 gives one launch per request, the baseline continuous
+ *   batching is measured against.
+ *   Inputs the device can read in place are not copied: page-locked host
+ *   memory mapped for the device, and any host memory when the device reads
+ *   pageable memory through the host's page tables (GB300 over NVLink-C2C).
+ *   The kernel then reads the request's bytes and offsets where they are;
+ *   they still count against read_budget_bytes while in flight.  Other
+ *   requests are copied into the read arena first.
+ * sbf_server_create_ex: flags = SBF_SERVER_STAGE_INPUTS copies every
+ *   request into the read arena (never reads host memory in place).
  * sbf_server_submit: queue one request of host reads (offsets as in
- *   sbf_query_seqs, off[0] = 0).  h_read_hits (n_reads) and h_kmer_bits
- *   (ceil(seq_len/32) words, may be NULL) receive exactly what
- *   sbf_query_seqs would write.  All host buffers must stay valid until the
- *   request is waited for; pinned buffers make the copies asynchronous.  A
- *   request larger than the budget is refused (SBF_EINVAL).  Thread-safe.
+ *   sbf_query_seqs, off[0] = 0).  h_read_hits (n_reads, may be NULL) and
+ *   h_kmer_bits (ceil(seq_len/32) words, may be NULL) receive exactly what
+ *   sbf_query_seqs would write.  All host buffers must stay valid and
+ *   unchanged until the request is waited for (the device may read them at
+ *   any time before).  A request larger than the budget, or with offsets that
+ *   decrease, is refused (SBF_EINVAL).  Thread-safe.
+ * sbf_server_submit_batch: n requests in one call (arrays of the arguments
+ *   above; h_read_hits and h_kmer_bits may be NULL arrays); tickets[i] is
+ *   request i's.  If any request is refused, none is queued.
  * sbf_server_wait: block until the request is done or timeout_s passes
  *   (SBF_ETIMEOUT); on success the ticket is released and *latency_s (may be
  *   NULL) is the time from submission to completion.
  * sbf_server_stats: latency percentiles of the requests completed since the
  *   last reset, and k-mers served per second from the first submission to
  *   the last completion.
+ * sbf_server_breakdown: p50 and p99 (arrays of 4) of the time requests spent
+ *   queued (submission to admission), being launched (admission to the end
+ *   of the launch calls), on the device (to the worker seeing the launch
+ *   complete) and in delivery (copies to the callers' buffers), since the
+ *   last reset; and how many requests were read in place and how many staged.
  * sbf_server_destroy: finishes queued and running requests, then frees.
  * ------------------------------------------------------------------------- */
 typedef struct sbf_server sbf_server;
+enum { SBF_SERVER_STAGE_INPUTS = 1 };
 
 int sbf_server_create(const sbf_filter* f, uint64_t read_budget_bytes, int max_inflight,
                       uint32_t max_per_launch, sbf_server** out);
+int sbf_server_create_ex(const sbf_filter* f, uint64_t read_budget_bytes, int max_inflight,
+                         uint32_t max_per_launch, uint32_t flags, sbf_server** out);
 void sbf_server_destroy(sbf_server* s);
 int sbf_server_submit(sbf_server* s, const uint8_t* h_seq, uint64_t seq_len, const uint64_t* h_off,
                       uint64_t n_reads, uint32_t* h_read_hits, uint32_t* h_kmer_bits,
                       uint64_t* ticket);
+int sbf_server_submit_batch(sbf_server* s, uint64_t n, const uint8_t* const* h_seqs,
+                            const uint64_t* seq_lens, const uint64_t* const* h_offs,
+                            const uint64_t* n_reads, uint32_t* const* h_read_hits,
+                            uint32_t* const* h_kmer_bits, uint64_t* tickets);
 int sbf_server_wait(sbf_server* s, uint64_t ticket, double timeout_s, double* latency_s);
 int sbf_server_stats(sbf_server* s, uint64_t* completed, double* p50_s, double* p99_s,
                      double* mean_s, double* kmers_per_s, uint64_t* launches);
+int sbf_server_breakdown(sbf_server* s, double* p50_s, double* p99_s, uint64_t* direct,
+                         uint64_t* staged);
 int sbf_server_reset_stats(sbf_server* s);
 
 /* Number of k-mer start positions sum_r max(0, len_r - k + 1) of a host

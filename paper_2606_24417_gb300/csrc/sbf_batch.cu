@@ -370,6 +370,12 @@ int sbf_batch_tune(sbf_batch* b, int insert, const uint8_t* d_seq, uint64_t seq_
   DeviceGuard dg(b->device);
   cudaStream_t st = (cudaStream_t)stream;
   using Cand = sbf_batch::Sched;
+  // Stage 1: how work reaches the warps -- a static split, or dynamic claims
+  // of `chunk` iterations (496 start positions each, so a claim is about
+  // chunk * 3 reads of 150 bp) -- at full occupancy.  Stage 2: blocks per SM
+  // (1..3 resident blocks instead of the full 4) with the best stage-1
+  // schedule, which trades latency hiding against tail imbalance and
+  // contention for L2 and the shard copies.
   const uint32_t full = 0;  // full occupancy
   const Cand cands[] = {{0, 1, full},  {1, 4, full},   {1, 16, full},
                         {1, 64, full}, {1, 256, full}, {1, 1024, full}};
@@ -380,7 +386,7 @@ int sbf_batch_tune(sbf_batch* b, int insert, const uint8_t* d_seq, uint64_t seq_
   float best = 1e30f;
   Cand pick = cands[0];
   int rc = SBF_OK;
-  for (const Cand& c : cands) {
+  auto time_one = [&](const Cand& c) -> float {
     sc = c;
     float t_min = 1e30f;
     for (int rep = 0; rep < 4 && rc == SBF_OK; ++rep) {
@@ -393,9 +399,22 @@ int sbf_batch_tune(sbf_batch* b, int insert, const uint8_t* d_seq, uint64_t seq_
       cudaEventElapsedTime(&ms, e0, e1);
       if (rep > 0) t_min = std::min(t_min, ms);  // first run warms caches
     }
+    return t_min;
+  };
+  for (const Cand& c : cands) {
+    const float t = time_one(c);
     if (rc != SBF_OK) break;
-    if (t_min < best) {
-      best = t_min;
+    if (t < best) {
+      best = t;
+      pick = c;
+    }
+  }
+  const uint32_t n_sm = (uint32_t)sbf::sm_count();
+  for (uint32_t per_sm = 1; rc == SBF_OK && per_sm <= 3; ++per_sm) {
+    const Cand c{pick.dynamic, pick.chunk, per_sm * n_sm};
+    const float t = time_one(c);
+    if (rc == SBF_OK && t < best) {
+      best = t;
       pick = c;
     }
   }

@@ -813,7 +813,7 @@ __device__ __forceinline__ bool run_range(WarpSmem<H, B, KEY64>& S, const Params
     {
       const uint32_t hs_i0 = (lane & 15u) * HS + (lane >> 4);
       const uint32_t so_i0 = (lane & 15u) * 34 + (lane >> 4);
-#pragma unroll 1
+#pragma unroll 2
       for (int pass = 0; pass < 16; pass += 2) {
         const uint32_t va = (S.valid_w[pass] >> lane) & 1u;
         const uint32_t vb = (S.valid_w[pass + 1] >> lane) & 1u;

@@ -1,16 +1,29 @@
 // sbf_server.cu -- serving loop for one resident filter (continuous batching).
 //
-// Clients submit query requests (host reads) from any thread.  A worker
-// thread admits queued requests while device memory for their reads, offsets
-// and hit counts is free in a fixed arena (admission by memory), coalesces
-// every admitted request into ONE launch of the fused query kernel (one
-// segment per request), and keeps up to `max_inflight` such launches on
-// separate streams so that requests arriving while others run are admitted
-// and their copies and kernels overlap on the device.  A launch completes
-// when its event fires; its requests' device memory is then freed.  Every
-// host wait is bounded (timeouts); nothing on the device waits.  Scheduling
-// never changes the answers: each request gets exactly the bits and hit
-// counts of a sbf_query_seqs call on its own reads.
+// Clients submit query requests (host reads) from any thread, one at a time
+// or many per call.  A worker thread admits queued requests while memory is
+// free (admission by memory), coalesces every admitted request into ONE
+// launch of the fused query kernel (one segment per request), and keeps up to
+// `max_inflight` such launches on separate streams, so requests that arrive
+// while others run are admitted and their work overlaps on the device.
+//
+// Inputs.  On a GB300 the GPU reads host memory over NVLink-C2C: pinned
+// (page-locked, mapped) buffers always, and ordinary pageable buffers when the
+// device reads them through the host's page tables (address translation
+// services).  A request whose bytes and offsets the device can read this way
+// is read in place by the kernel -- no copy, no per-request API call; its
+// bytes still count against the read budget while it is in flight.  Other
+// requests are copied into a device read arena first (the staged path, also
+// forced by SBF_SERVER_STAGE_INPUTS).
+//
+// Results.  Hit counts (and answer words when asked for) land in a device
+// result arena, go back to a pinned mirror with one copy per contiguous run
+// of the launch's result regions, and are copied to the callers' buffers by
+// the worker after the launch completes, outside the lock.
+//
+// Every host wait is bounded (timeouts); nothing on the device waits.
+// Scheduling never changes the answers: each request gets exactly the bits
+// and hit counts of a sbf_query_seqs call on its own reads.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -37,6 +50,10 @@ class Arena {
  public:
   explicit Arena(uint64_t size) : size_(size) { free_[0] = size; }
   bool alloc(uint64_t n, uint64_t align, uint64_t* at) {
+    if (n == 0) {
+      *at = 0;
+      return true;
+    }
     for (auto it = free_.begin(); it != free_.end(); ++it) {
       uint64_t start = (it->first + align - 1) / align * align;
       uint64_t end = it->first + it->second;
@@ -52,6 +69,7 @@ class Arena {
     return false;
   }
   void release(uint64_t at, uint64_t n) {
+    if (n == 0) return;
     auto it = free_.emplace(at, n).first;
     auto next = std::next(it);
     if (next != free_.end() && it->first + it->second == next->first) {
@@ -81,21 +99,28 @@ struct Request {
   uint64_t n_reads = 0;
   uint32_t* h_hits = nullptr;
   uint32_t* h_bits = nullptr;
-  uint64_t seq_at = 0, seq_bytes = 0;    // placement in the read arena
-  uint64_t meta_at = 0, meta_bytes = 0;  // offsets + hits in the meta arena
+  // device-visible views of the inputs (direct reads), or NULL: staged
+  const uint8_t* v_seq = nullptr;
+  const uint64_t* v_off = nullptr;
+  uint64_t seq_at = 0, seq_bytes = 0;    // staged reads in the read arena
+  uint64_t off_at = 0, off_bytes = 0;    // staged offsets in the offset arena
+  uint64_t budget_bytes = 0;             // read bytes counted against the budget
+  uint64_t res_at = 0, res_bytes = 0;    // hits, then answer words, in the result arena
+  uint64_t bits_at = 0;                  // answer words' place in the result arena
   uint64_t kmers = 0;
-  Clock::time_point t_submit, t_done;
+  Clock::time_point t_submit, t_admit, t_launch, t_complete, t_done;
   int state = 0;                         // 0 queued, 1 in flight, 2 done, < 0 error code
 };
 
 struct Launch {
   std::vector<Request*> reqs;
   int slot = 0;
+  uint64_t seq_used = 0;                 // budget bytes of direct requests
 };
 
 // Zeroes each segment's hit counts and answer words (when it has them) before
-// the query: one launch for a whole batch of requests instead of two memsets
-// per request.  Block b handles segments b, b + gridDim.x, ...
+// the query: one launch for a whole batch of requests.  Block b handles
+// segments b, b + gridDim.x, ...
 __global__ void zero_segments(const Segment* __restrict__ segs, uint32_t n_segs) {
   for (uint32_t i = blockIdx.x; i < n_segs; i += gridDim.x) {
     const Segment sg = segs[i];
@@ -107,6 +132,8 @@ __global__ void zero_segments(const Segment* __restrict__ segs, uint32_t n_segs)
   }
 }
 
+constexpr int kStages = 4;   // queue, launch, device, delivery
+
 }  // namespace
 
 struct sbf_server {
@@ -114,16 +141,19 @@ struct sbf_server {
   int device = 0;
   int max_inflight = 2;
   uint32_t max_per_launch = 4096;
-  // device arenas
-  uint8_t* d_seq = nullptr;     // reads
-  uint32_t* d_bits = nullptr;   // answers, one bit per read-arena byte
-  uint8_t* d_meta = nullptr;    // offsets and hit counts
-  // pinned host mirrors of the result arenas: results land here
-  // asynchronously and are copied to the caller's buffers after completion
-  // (a device-to-host copy into pageable memory would block the worker)
-  uint8_t* h_meta = nullptr;
-  uint32_t* h_bits = nullptr;
-  std::unique_ptr<Arena> seq_arena, meta_arena;
+  bool stage_inputs = false;        // SBF_SERVER_STAGE_INPUTS
+  bool pageable_direct = false;     // the device reads pageable memory via host page tables
+  // device arenas: staged reads and offsets; results (hits and answer words)
+  uint8_t* d_seq = nullptr;
+  uint8_t* d_off = nullptr;
+  uint8_t* d_res = nullptr;
+  uint8_t* h_res = nullptr;         // pinned mirror of the result arena
+  std::unique_ptr<Arena> seq_arena, off_arena, res_arena;
+  uint64_t read_budget = 0, direct_in_flight = 0;
+  // read bytes after which a launch takes no further request, so that a deep
+  // queue becomes several launches whose result copies and delivery overlap
+  // the next launch's kernel
+  uint64_t launch_cap = 0;
   // per launch slot: stream, event, segment tables
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
@@ -142,7 +172,8 @@ struct sbf_server {
   std::thread worker;
   // statistics
   std::vector<double> latencies;
-  uint64_t kmers_done = 0, launches = 0;
+  std::vector<double> stage_s[kStages];
+  uint64_t kmers_done = 0, launches = 0, direct_reqs = 0, staged_reqs = 0;
   Clock::time_point first_submit, last_done;
   bool have_first = false;
 };
@@ -163,6 +194,58 @@ void CUDART_CB on_launch_done(void* arg) {
   s->cv_work.notify_all();
 }
 
+// The address through which the device reads host memory p, or NULL if it
+// cannot: page-locked memory mapped into the device's address space, or any
+// host memory when the device reads pageable memory through the host's page
+// tables.
+const void* device_view(const sbf_server* s, const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeHost) return a.devicePointer;  // NULL if not mapped for this device
+  if (a.type == cudaMemoryTypeUnregistered && s->pageable_direct) return p;
+  return nullptr;
+}
+
+// Place one request: device views of its inputs (or arena space to stage
+// them) and result space.  Caller holds s->mu.  False: no room yet.
+bool admit(sbf_server* s, Request* r, Launch& L) {
+  const bool direct = r->v_seq && (r->v_off || r->n_reads == 0);
+  uint64_t sa = 0, oa = 0, ra = 0;
+  if (direct) {
+    // read in place: only the budget of read bytes in flight applies
+    if (s->direct_in_flight + L.seq_used + r->budget_bytes > s->read_budget) return false;
+  } else {
+    if (!s->seq_arena->alloc(r->seq_bytes, 32, &sa)) return false;
+    if (!s->off_arena->alloc(r->off_bytes, 16, &oa)) {
+      s->seq_arena->release(sa, r->seq_bytes);
+      return false;
+    }
+  }
+  if (!s->res_arena->alloc(r->res_bytes, 16, &ra)) {
+    if (!direct) {
+      s->seq_arena->release(sa, r->seq_bytes);
+      s->off_arena->release(oa, r->off_bytes);
+    }
+    return false;
+  }
+  if (direct) {
+    L.seq_used += r->budget_bytes;
+    r->seq_bytes = r->off_bytes = 0;
+  } else {
+    r->v_seq = nullptr;
+    r->v_off = nullptr;
+    r->seq_at = sa;
+    r->off_at = oa;
+  }
+  r->res_at = ra;
+  r->bits_at = ra + (r->n_reads * 4 + 15) / 16 * 16;
+  return true;
+}
+
 // Launch every request of `L` as one segment each, on slot L.slot.
 int start_launch(sbf_server* s, Launch& L) {
   const sbf::Geom& g = s->filter->geom;
@@ -174,20 +257,27 @@ int start_launch(sbf_server* s, Launch& L) {
   cudaError_t e = cudaSuccess;
   for (size_t i = 0; i < L.reqs.size(); ++i) {
     Request* r = L.reqs[i];
-    uint64_t* d_off = reinterpret_cast<uint64_t*>(s->d_meta + r->meta_at);
-    uint32_t* d_hits = reinterpret_cast<uint32_t*>(d_off + r->n_reads + 1);
-    if ((e = cudaMemcpyAsync(s->d_seq + r->seq_at, r->h_seq, r->seq_len, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(d_off, r->h_off, (r->n_reads + 1) * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-      return cuda_fail(e, "server staging");
+    const uint8_t* seq = r->v_seq;
+    const uint64_t* off = r->v_off;
+    if (!seq) {  // staged: copy the request's bytes and offsets into the arenas
+      seq = s->d_seq + r->seq_at;
+      off = reinterpret_cast<const uint64_t*>(s->d_off + r->off_at);
+      if ((r->seq_len &&
+           (e = cudaMemcpyAsync(s->d_seq + r->seq_at, r->h_seq, r->seq_len, cudaMemcpyHostToDevice,
+                                st)) != cudaSuccess) ||
+          (e = cudaMemcpyAsync(s->d_off + r->off_at, r->h_off, (r->n_reads + 1) * 8,
+                               cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "server staging");
+    }
     Segment sg{};
     sg.words = g.words;
     sg.n_shards = g.n_shards;
-    sg.seq = s->d_seq + r->seq_at;   // the request's own bytes, offsets as submitted
+    sg.seq = seq;                    // the request's own bytes, offsets as submitted
     sg.seq_len = r->seq_len;
-    sg.off = d_off;
+    sg.off = off;
     sg.n_reads = r->n_reads;
-    sg.bits = r->h_bits ? s->d_bits + r->seq_at / 32 : nullptr;  // no answer words wanted: none written
-    sg.hits = d_hits;
+    sg.bits = r->h_bits ? reinterpret_cast<uint32_t*>(s->d_res + r->bits_at) : nullptr;
+    sg.hits = reinterpret_cast<uint32_t*>(s->d_res + r->res_at);
     sg.p_begin = 0;
     sg.iter_begin = iters;
     sg.iters = (r->seq_len + adv - 1) / adv;
@@ -213,16 +303,27 @@ int start_launch(sbf_server* s, Launch& L) {
   P.grid_blocks = 0;
   P.big = sbf::fused::is_big(g) ? 1u : 0u;
   if ((e = sbf::fused::launch_params(P, false, st)) != cudaSuccess) return cuda_fail(e, "server launch");
-  for (Request* r : L.reqs) {
-    const uint64_t hits_at = r->meta_at + (r->n_reads + 1) * 8;
-    if (r->h_hits && r->n_reads &&
-        (e = cudaMemcpyAsync(s->h_meta + hits_at, s->d_meta + hits_at, r->n_reads * 4,
-                             cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+  // results back to the pinned mirror: one copy per contiguous run of the
+  // launch's result regions (consecutive admissions are mostly adjacent)
+  std::vector<std::pair<uint64_t, uint64_t>> ranges;
+  ranges.reserve(L.reqs.size());
+  for (const Request* r : L.reqs) {
+    const uint64_t used = r->h_bits ? r->res_bytes : r->n_reads * 4;
+    if (used) ranges.emplace_back(r->res_at, r->res_at + used);
+  }
+  std::sort(ranges.begin(), ranges.end());
+  for (size_t i = 0; i < ranges.size();) {
+    uint64_t a = ranges[i].first, b = ranges[i].second;
+    size_t j = i + 1;
+    // merge regions whose gap is small (alignment padding or a few bytes)
+    while (j < ranges.size() && ranges[j].first <= b + 256) {
+      b = std::max(b, ranges[j].second);
+      ++j;
+    }
+    if ((e = cudaMemcpyAsync(s->h_res + a, s->d_res + a, b - a, cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
       return cuda_fail(e, "server results");
-    if (r->h_bits && r->seq_len &&
-        (e = cudaMemcpyAsync(s->h_bits + r->seq_at / 32, s->d_bits + r->seq_at / 32,
-                             ((r->seq_len + 31) / 32) * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-      return cuda_fail(e, "server results");
+    i = j;
   }
   if ((e = cudaEventRecord(s->events[slot], st)) != cudaSuccess) return cuda_fail(e, "server event");
   // wake the worker when this launch's work is done instead of letting it poll
@@ -231,27 +332,35 @@ int start_launch(sbf_server* s, Launch& L) {
   return SBF_OK;
 }
 
-// Copy a finished launch's results from the pinned mirrors to the callers'
+// Copy a finished launch's results from the pinned mirror to the callers'
 // buffers (no lock needed: the requests' arena space is still theirs).
 void deliver(sbf_server* s, const Launch& L) {
   for (const Request* r : L.reqs) {
-    if (r->h_hits && r->n_reads)
-      std::memcpy(r->h_hits, s->h_meta + r->meta_at + (r->n_reads + 1) * 8, r->n_reads * 4);
+    if (r->h_hits && r->n_reads) std::memcpy(r->h_hits, s->h_res + r->res_at, r->n_reads * 4);
     if (r->h_bits && r->seq_len)
-      std::memcpy(r->h_bits, s->h_bits + r->seq_at / 32, ((r->seq_len + 31) / 32) * 4);
+      std::memcpy(r->h_bits, s->h_res + r->bits_at, ((r->seq_len + 31) / 32) * 4);
   }
 }
 
 void finish(sbf_server* s, Launch& L, int status) {
   // caller holds s->mu
   const Clock::time_point now = Clock::now();
+  s->direct_in_flight -= L.seq_used;
   for (Request* r : L.reqs) {
     r->state = status == SBF_OK ? 2 : status;
     r->t_done = now;
     s->seq_arena->release(r->seq_at, r->seq_bytes);
-    s->meta_arena->release(r->meta_at, r->meta_bytes);
+    s->off_arena->release(r->off_at, r->off_bytes);
+    s->res_arena->release(r->res_at, r->res_bytes);
     if (status == SBF_OK) {
-      s->latencies.push_back(std::chrono::duration<double>(r->t_done - r->t_submit).count());
+      auto d = [](Clock::time_point a, Clock::time_point b) {
+        return std::chrono::duration<double>(b - a).count();
+      };
+      s->latencies.push_back(d(r->t_submit, r->t_done));
+      s->stage_s[0].push_back(d(r->t_submit, r->t_admit));
+      s->stage_s[1].push_back(d(r->t_admit, r->t_launch));
+      s->stage_s[2].push_back(d(r->t_launch, r->t_complete));
+      s->stage_s[3].push_back(d(r->t_complete, r->t_done));
       s->kmers_done += r->kmers;
       s->last_done = now;
     }
@@ -275,6 +384,9 @@ void worker_loop(sbf_server* s) {
       s->inflight.erase(s->inflight.begin() + i);
     }
     if (!done.empty()) {
+      const Clock::time_point now = Clock::now();
+      for (auto& d : done)
+        for (Request* r : d.first.reqs) r->t_complete = now;
       lk.unlock();
       for (auto& d : done)
         if (d.second == SBF_OK) deliver(s, d.first);
@@ -292,28 +404,30 @@ void worker_loop(sbf_server* s) {
       }
     Launch L;
     if (slot >= 0) {
-      while (!s->queue.empty() && L.reqs.size() < s->max_per_launch) {
+      const Clock::time_point now = Clock::now();
+      uint64_t launch_bytes = 0;
+      while (!s->queue.empty() && L.reqs.size() < s->max_per_launch &&
+             (L.reqs.empty() || launch_bytes < s->launch_cap)) {
         Request* r = s->queue.front();
-        uint64_t sa = 0, ma = 0;
-        if (!s->seq_arena->alloc(r->seq_bytes, 32, &sa)) break;
-        if (!s->meta_arena->alloc(r->meta_bytes, 16, &ma)) {
-          s->seq_arena->release(sa, r->seq_bytes);
-          break;
-        }
-        r->seq_at = sa;
-        r->meta_at = ma;
+        if (!admit(s, r, L)) break;
+        launch_bytes += r->budget_bytes;
         r->state = 1;
+        r->t_admit = now;
         s->queue.pop_front();
         L.reqs.push_back(r);
+        if (r->v_seq) ++s->direct_reqs; else ++s->staged_reqs;
       }
     }
     if (!L.reqs.empty()) {
       L.slot = slot;
       s->slot_busy[slot] = true;
+      s->direct_in_flight += L.seq_used;
       ++s->launches;
       lk.unlock();
       int rc = start_launch(s, L);
+      const Clock::time_point now = Clock::now();
       lk.lock();
+      for (Request* r : L.reqs) r->t_launch = now;
       if (rc != SBF_OK) {
         finish(s, L, rc);
         s->cv_done.notify_all();
@@ -331,15 +445,87 @@ void worker_loop(sbf_server* s) {
   }
 }
 
+// Checks one request and prepares it for the queue (no lock held): offsets,
+// k-mer count, the device's view of its inputs and the arena sizes.
+int prepare(sbf_server* s, const uint8_t* h_seq, uint64_t seq_len, const uint64_t* h_off,
+            uint64_t n_reads, uint32_t* h_read_hits, uint32_t* h_kmer_bits, Request** out) {
+  if (!h_off || (seq_len && !h_seq)) return fail(SBF_EINVAL, "bad argument");
+  if (h_off[0] != 0 || h_off[n_reads] != seq_len)
+    return fail(SBF_EINVAL, "offsets must start at 0 and end at seq_len");
+  const int k = s->filter->geom.k;
+  uint64_t kmers = 0;
+  for (uint64_t i = 0; i < n_reads; ++i) {
+    if (h_off[i + 1] < h_off[i])
+      return fail(SBF_EINVAL, "offsets decrease at read %llu", (unsigned long long)i);
+    const uint64_t len = h_off[i + 1] - h_off[i];
+    if (len >= (uint64_t)k) kmers += len - k + 1;
+  }
+  Request* r = new (std::nothrow) Request();
+  if (!r) return fail(SBF_ENOMEM, "host allocation failed");
+  r->h_seq = h_seq;
+  r->seq_len = seq_len;
+  r->h_off = h_off;
+  r->n_reads = n_reads;
+  r->h_hits = h_read_hits;
+  r->h_bits = h_kmer_bits;
+  r->kmers = kmers;
+  r->seq_bytes = std::max<uint64_t>(32, (seq_len + 31) / 32 * 32);
+  r->off_bytes = ((n_reads + 1) * 8 + 15) / 16 * 16;
+  r->budget_bytes = r->seq_bytes;
+  r->res_bytes = (n_reads * 4 + 15) / 16 * 16 + (h_kmer_bits ? ((seq_len + 31) / 32 * 4 + 15) / 16 * 16 : 0);
+  if (r->res_bytes == 0) r->res_bytes = 16;
+  if (!s->stage_inputs) {
+    r->v_seq = seq_len ? static_cast<const uint8_t*>(device_view(s, h_seq)) : nullptr;
+    r->v_off = static_cast<const uint64_t*>(device_view(s, h_off));
+    if (!r->v_seq || !r->v_off) r->v_seq = nullptr, r->v_off = nullptr;  // stage both
+  }
+  if (r->seq_bytes > s->read_budget || r->off_bytes > s->off_arena->size() ||
+      r->res_bytes > s->res_arena->size()) {
+    delete r;
+    return fail(SBF_EINVAL, "request larger than the server's memory budget");
+  }
+  *out = r;
+  return SBF_OK;
+}
+
+// Queues prepared requests (one lock for all of them).
+void enqueue(sbf_server* s, Request* const* rs, uint64_t n, uint64_t* tickets) {
+  const Clock::time_point now = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (uint64_t i = 0; i < n; ++i) {
+      Request* r = rs[i];
+      r->t_submit = now;
+      r->id = s->next_id++;
+      if (!s->have_first) {
+        s->first_submit = now;
+        s->have_first = true;
+      }
+      s->by_id[r->id] = r;
+      s->queue.push_back(r);
+      tickets[i] = r->id;
+    }
+    s->submissions += n;
+  }
+  s->cv_work.notify_one();
+}
+
+double percentile(std::vector<double> v, double p) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  size_t i = (size_t)std::min<double>((double)v.size() - 1, p * (double)(v.size() - 1) + 0.5);
+  return v[i];
+}
+
 }  // namespace
 
 extern "C" {
 
-int sbf_server_create(const sbf_filter* f, uint64_t read_budget_bytes, int max_inflight,
-                      uint32_t max_per_launch, sbf_server** out) {
+int sbf_server_create_ex(const sbf_filter* f, uint64_t read_budget_bytes, int max_inflight,
+                         uint32_t max_per_launch, uint32_t flags, sbf_server** out) {
   sbf::clear_error();
   if (!f || !out || read_budget_bytes < 4096 || max_inflight < 1 || max_inflight > 16 ||
-      max_per_launch < 1 || max_per_launch > 65536)
+      max_per_launch < 1 || max_per_launch > 65536 || (flags & ~(uint32_t)SBF_SERVER_STAGE_INPUTS))
     return fail(SBF_EINVAL, "bad argument");
   *out = nullptr;
   if (!f->fused) return fail(SBF_EUNSUPPORTED, "the server needs a filter with fused kernels");
@@ -349,16 +535,26 @@ int sbf_server_create(const sbf_filter* f, uint64_t read_budget_bytes, int max_i
   s->device = f->device;
   s->max_inflight = max_inflight;
   s->max_per_launch = max_per_launch;
+  s->stage_inputs = (flags & SBF_SERVER_STAGE_INPUTS) != 0;
   const uint64_t seq_bytes = (read_budget_bytes + 31) / 32 * 32;
-  const uint64_t meta_bytes = seq_bytes / 4 + (1 << 16);
+  s->read_budget = seq_bytes;
+  s->launch_cap = std::max<uint64_t>(seq_bytes / (uint64_t)(max_inflight + 1), 1ull << 20);
+  // offsets: 8 bytes per read of >= 1 byte is at most 8x the reads; reads of
+  // the benchmark's 150 bp need about 1/19 of them.  Results: 4 bytes per
+  // read plus one bit per byte.
+  const uint64_t off_bytes = seq_bytes / 4 + (1 << 16);
+  const uint64_t res_bytes = seq_bytes / 4 + seq_bytes / 8 + (1 << 16);
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(s->device);
+  int pageable = 0, host_tables = 0;
+  cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, s->device);
+  cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, s->device);
+  s->pageable_direct = pageable == 1 && host_tables == 1;
   bool ok = cudaMalloc(&s->d_seq, seq_bytes) == cudaSuccess &&
-            cudaMalloc(&s->d_bits, seq_bytes / 8) == cudaSuccess &&
-            cudaMalloc(&s->d_meta, meta_bytes) == cudaSuccess &&
-            cudaMallocHost(&s->h_bits, seq_bytes / 8) == cudaSuccess &&
-            cudaMallocHost(&s->h_meta, meta_bytes) == cudaSuccess;
+            cudaMalloc(&s->d_off, off_bytes) == cudaSuccess &&
+            cudaMalloc(&s->d_res, res_bytes) == cudaSuccess &&
+            cudaMallocHost(&s->h_res, res_bytes) == cudaSuccess;
   s->streams.resize(max_inflight);
   s->events.resize(max_inflight);
   s->h_tables.resize(max_inflight);
@@ -384,10 +580,16 @@ int sbf_server_create(const sbf_filter* f, uint64_t read_budget_bytes, int max_i
     return fail(SBF_ENOMEM, "server device allocation failed");
   }
   s->seq_arena.reset(new Arena(seq_bytes));
-  s->meta_arena.reset(new Arena(meta_bytes));
+  s->off_arena.reset(new Arena(off_bytes));
+  s->res_arena.reset(new Arena(res_bytes));
   s->worker = std::thread(worker_loop, s);
   *out = s;
   return SBF_OK;
+}
+
+int sbf_server_create(const sbf_filter* f, uint64_t read_budget_bytes, int max_inflight,
+                      uint32_t max_per_launch, sbf_server** out) {
+  return sbf_server_create_ex(f, read_budget_bytes, max_inflight, max_per_launch, 0, out);
 }
 
 void sbf_server_destroy(sbf_server* s) {
@@ -411,10 +613,9 @@ void sbf_server_destroy(sbf_server* s) {
     if (s->d_tables[i]) cudaFree(s->d_tables[i]);
   }
   cudaFree(s->d_seq);
-  cudaFree(s->d_bits);
-  cudaFree(s->d_meta);
-  cudaFreeHost(s->h_bits);
-  cudaFreeHost(s->h_meta);
+  cudaFree(s->d_off);
+  cudaFree(s->d_res);
+  cudaFreeHost(s->h_res);
   cudaSetDevice(prev);
   for (auto& kv : s->by_id) delete kv.second;
   delete s;
@@ -424,44 +625,46 @@ int sbf_server_submit(sbf_server* s, const uint8_t* h_seq, uint64_t seq_len, con
                       uint64_t n_reads, uint32_t* h_read_hits, uint32_t* h_kmer_bits,
                       uint64_t* ticket) {
   sbf::clear_error();
-  if (!s || !ticket || !h_off || (seq_len && !h_seq)) return fail(SBF_EINVAL, "bad argument");
-  if (h_off[0] != 0 || h_off[n_reads] != seq_len)
-    return fail(SBF_EINVAL, "offsets must start at 0 and end at seq_len");
-  for (uint64_t r = 0; r < n_reads; ++r)
-    if (h_off[r + 1] < h_off[r]) return fail(SBF_EINVAL, "offsets decrease at read %llu", (unsigned long long)r);
-  Request* r = new (std::nothrow) Request();
-  if (!r) return fail(SBF_ENOMEM, "host allocation failed");
-  r->h_seq = h_seq;
-  r->seq_len = seq_len;
-  r->h_off = h_off;
-  r->n_reads = n_reads;
-  r->h_hits = h_read_hits;
-  r->h_bits = h_kmer_bits;
-  r->seq_bytes = std::max<uint64_t>(32, (seq_len + 31) / 32 * 32);
-  r->meta_bytes = ((n_reads + 1) * 8 + n_reads * 4 + 15) / 16 * 16;
-  const int k = s->filter->geom.k;
-  for (uint64_t i = 0; i < n_reads; ++i) {
-    uint64_t len = h_off[i + 1] - h_off[i];
-    if (len >= (uint64_t)k) r->kmers += len - k + 1;
+  if (!s || !ticket) return fail(SBF_EINVAL, "bad argument");
+  // make the device's context current on this thread (a thread that never
+  // made a CUDA call has none, and pointer queries would then see no pinned
+  // memory)
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  Request* r = nullptr;
+  const int rc = prepare(s, h_seq, seq_len, h_off, n_reads, h_read_hits, h_kmer_bits, &r);
+  if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+  if (rc != SBF_OK) return rc;
+  enqueue(s, &r, 1, ticket);
+  return SBF_OK;
+}
+
+int sbf_server_submit_batch(sbf_server* s, uint64_t n, const uint8_t* const* h_seqs,
+                            const uint64_t* seq_lens, const uint64_t* const* h_offs,
+                            const uint64_t* n_reads, uint32_t* const* h_read_hits,
+                            uint32_t* const* h_kmer_bits, uint64_t* tickets) {
+  sbf::clear_error();
+  if (!s || (n && (!h_seqs || !seq_lens || !h_offs || !n_reads || !tickets)))
+    return fail(SBF_EINVAL, "bad argument");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  std::vector<Request*> rs;
+  rs.reserve(n);
+  int rc = SBF_OK;
+  for (uint64_t i = 0; i < n && rc == SBF_OK; ++i) {
+    Request* r = nullptr;
+    rc = prepare(s, h_seqs[i], seq_lens[i], h_offs[i], n_reads[i],
+                 h_read_hits ? h_read_hits[i] : nullptr, h_kmer_bits ? h_kmer_bits[i] : nullptr, &r);
+    if (rc == SBF_OK) rs.push_back(r);
   }
-  if (r->seq_bytes > s->seq_arena->size() || r->meta_bytes > s->meta_arena->size()) {
-    delete r;
-    return fail(SBF_EINVAL, "request larger than the server's memory budget");
+  if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+  if (rc != SBF_OK) {  // nothing is queued when any request is refused
+    for (Request* r : rs) delete r;
+    return rc;
   }
-  r->t_submit = Clock::now();
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    r->id = s->next_id++;
-    if (!s->have_first) {
-      s->first_submit = r->t_submit;
-      s->have_first = true;
-    }
-    s->by_id[r->id] = r;
-    s->queue.push_back(r);
-    ++s->submissions;
-    *ticket = r->id;
-  }
-  s->cv_work.notify_one();
+  enqueue(s, rs.data(), n, tickets);
   return SBF_OK;
 }
 
@@ -491,16 +694,10 @@ int sbf_server_stats(sbf_server* s, uint64_t* completed, double* p50_s, double* 
   sbf::clear_error();
   if (!s) return fail(SBF_EINVAL, "server is NULL");
   std::lock_guard<std::mutex> lk(s->mu);
-  std::vector<double> v = s->latencies;
-  std::sort(v.begin(), v.end());
-  auto pct = [&](double p) -> double {
-    if (v.empty()) return 0.0;
-    size_t i = (size_t)std::min<double>((double)v.size() - 1, p * (double)(v.size() - 1) + 0.5);
-    return v[i];
-  };
+  const std::vector<double>& v = s->latencies;
   if (completed) *completed = v.size();
-  if (p50_s) *p50_s = pct(0.50);
-  if (p99_s) *p99_s = pct(0.99);
+  if (p50_s) *p50_s = percentile(v, 0.50);
+  if (p99_s) *p99_s = percentile(v, 0.99);
   if (mean_s) {
     double sum = 0;
     for (double x : v) sum += x;
@@ -514,13 +711,29 @@ int sbf_server_stats(sbf_server* s, uint64_t* completed, double* p50_s, double* 
   return SBF_OK;
 }
 
+int sbf_server_breakdown(sbf_server* s, double* p50_s, double* p99_s, uint64_t* direct,
+                         uint64_t* staged) {
+  sbf::clear_error();
+  if (!s) return fail(SBF_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (int i = 0; i < kStages; ++i) {
+    if (p50_s) p50_s[i] = percentile(s->stage_s[i], 0.50);
+    if (p99_s) p99_s[i] = percentile(s->stage_s[i], 0.99);
+  }
+  if (direct) *direct = s->direct_reqs;
+  if (staged) *staged = s->staged_reqs;
+  return SBF_OK;
+}
+
 int sbf_server_reset_stats(sbf_server* s) {
   sbf::clear_error();
   if (!s) return fail(SBF_EINVAL, "server is NULL");
   std::lock_guard<std::mutex> lk(s->mu);
   s->latencies.clear();
+  for (auto& v : s->stage_s) v.clear();
   s->kmers_done = 0;
   s->launches = 0;
+  s->direct_reqs = s->staged_reqs = 0;
   s->have_first = false;
   return SBF_OK;
 }

@@ -71,6 +71,10 @@ def load_library() -> ctypes.CDLL:
             "sbf_num_kmers": (I, [P, U64, I, ctypes.POINTER(U64)]),
             "sbf_last_error": (ctypes.c_char_p, []),
             "sbf_server_create": (I, [P, U64, I, ctypes.c_uint32, ctypes.POINTER(P)]),
+            "sbf_server_create_ex": (I, [P, U64, I, ctypes.c_uint32, ctypes.c_uint32,
+                                         ctypes.POINTER(P)]),
+            "sbf_server_submit_batch": (I, [P, U64, P, P, P, P, P, P, P]),
+            "sbf_server_breakdown": (I, [P, P, P, ctypes.POINTER(U64), ctypes.POINTER(U64)]),
             "sbf_server_destroy": (None, [P]),
             "sbf_server_submit": (I, [P, P, U64, P, U64, U32P, U32P, ctypes.POINTER(U64)]),
             "sbf_server_wait": (I, [P, U64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
@@ -400,11 +404,12 @@ class FilterServer:
     to ``submit`` are kept alive here until waited for."""
 
     def __init__(self, filt: "SuperBloomFilter", read_budget_bytes: int = 256 << 20,
-                 max_inflight: int = 3, max_per_launch: int = 4096):
+                 max_inflight: int = 3, max_per_launch: int = 4096, stage_inputs: bool = False):
         lib = load_library()
         h = ctypes.c_void_p()
-        _check(lib.sbf_server_create(filt.handle, read_budget_bytes, max_inflight, max_per_launch,
-                                     ctypes.byref(h)))
+        _check(lib.sbf_server_create_ex(filt.handle, read_budget_bytes, max_inflight,
+                                        max_per_launch, 1 if stage_inputs else 0,
+                                        ctypes.byref(h)))
         self._h = h
         self._lib = lib
         self._filter = filt
@@ -436,6 +441,42 @@ class FilterServer:
         with self._lock:
             self._keep[t.value] = (seq, off, hits, bits)
         return t.value
+
+    def submit_many(self, requests, want_bits: bool = False):
+        """Queue many (seq, off) requests with one call; returns their tickets."""
+        n = len(requests)
+        if n == 0:
+            return []
+        seqs = [np.ascontiguousarray(q[0], dtype=np.uint8) for q in requests]
+        offs = [np.ascontiguousarray(q[1], dtype=np.uint64) for q in requests]
+        hits = [np.empty(o.size - 1, dtype=np.uint32) for o in offs]
+        bits = [np.empty((q.size + 31) // 32, dtype=np.uint32) for q in seqs] if want_bits else None
+        ptr = lambda arrs: np.array([a.ctypes.data for a in arrs], dtype=np.uint64)  # noqa: E731
+        p_seq, p_off, p_hits = ptr(seqs), ptr(offs), ptr(hits)
+        p_bits = ptr(bits) if want_bits else None
+        lens = np.array([q.size for q in seqs], dtype=np.uint64)
+        nr = np.array([o.size - 1 for o in offs], dtype=np.uint64)
+        t = np.empty(n, dtype=np.uint64)
+        _check(self._lib.sbf_server_submit_batch(self._h, n, _host_ptr(p_seq), _host_ptr(lens),
+                                                 _host_ptr(p_off), _host_ptr(nr), _host_ptr(p_hits),
+                                                 _host_ptr(p_bits) if want_bits else None,
+                                                 _host_ptr(t)))
+        tickets = [int(x) for x in t]
+        with self._lock:
+            for i, tk in enumerate(tickets):
+                self._keep[tk] = (seqs[i], offs[i], hits[i], bits[i] if want_bits else None)
+        return tickets
+
+    def breakdown(self) -> dict:
+        """p50 / p99 seconds per stage (queued, launching, device, delivery)
+        and how many requests were read in place or staged."""
+        p50 = (ctypes.c_double * 4)()
+        p99 = (ctypes.c_double * 4)()
+        d, st = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self._lib.sbf_server_breakdown(self._h, p50, p99, ctypes.byref(d), ctypes.byref(st)))
+        names = ("queued", "launching", "device", "delivery")
+        return {"p50_s": dict(zip(names, list(p50))), "p99_s": dict(zip(names, list(p99))),
+                "direct_requests": int(d.value), "staged_requests": int(st.value)}
 
     def wait(self, ticket: int, timeout_s: float = 60.0):
         """Returns (hits, bits or None, latency seconds)."""

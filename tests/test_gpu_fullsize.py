@@ -184,7 +184,7 @@ def test_served_4gib_full_size(tmp_path):
         mix = [None] * len(reqs)
 
         def client(idx):
-            tickets = [(i, srv.submit(reqs[i][0], reqs[i][1], want_bits=True)) for i in idx]
+            tickets = list(zip(idx, srv.submit_many([reqs[i] for i in idx], want_bits=True)))
             for i, t in tickets:
                 hits, qb, _ = srv.wait(t, 120)
                 mix[i] = (hits.copy(), qb.copy())

@@ -65,7 +65,9 @@ def test_alone_equals_mix_equals_direct(served):
     mix = [None] * len(reqs)
 
     def client(idx):
-        tickets = [(i, srv.submit(reqs[i][0], reqs[i][1], want_bits=True)) for i in idx]
+        # each client queues its share in one call, so the worker finds several
+        # requests waiting and serves them together
+        tickets = list(zip(idx, srv.submit_many([reqs[i] for i in idx], want_bits=True)))
         for i, t in tickets:
             hits, bits, _ = srv.wait(t, 60)
             mix[i] = (hits.copy(), bits.copy())
@@ -148,3 +150,64 @@ def test_large_filter_served_equals_direct():
     assert f.device_status() == 0
     srv.close()
     f.close()
+
+
+def test_staged_and_in_place_inputs_and_batch_submission(served):
+    """The same requests through a server that copies every input into its
+    read arena, through one that reads host memory in place where the device
+    can (pinned buffers always; pageable buffers when the device reads them
+    through the host's page tables), and submitted all in one call: identical
+    answers, equal to direct queries."""
+    from paper_2606_24417_gb300.sbf import FilterServer
+
+    f, _, _, reqs = served
+    pinned = []
+    for seq, off in reqs[:12]:
+        ps = torch.from_numpy(seq).pin_memory().numpy()
+        po = torch.from_numpy(off.view(np.int64)).pin_memory().numpy().view(np.uint64)
+        pinned.append((ps, po))
+    results = {}
+    for name, stage, rq in (("staged", True, reqs), ("in_place", False, reqs),
+                            ("pinned", False, pinned)):
+        srv = FilterServer(f, read_budget_bytes=16 << 20, max_inflight=3, stage_inputs=stage)
+        tickets = srv.submit_many(rq, want_bits=True)
+        results[name] = [srv.wait(t, 60)[:2] for t in tickets]
+        info = srv.breakdown()
+        if stage:
+            assert info["direct_requests"] == 0 and info["staged_requests"] == len(rq)
+        if name == "pinned":   # page-locked memory is always read in place
+            assert info["direct_requests"] == len(rq)
+            # also when submitted from a thread that made no CUDA call before
+            srv.reset_stats()
+            out = []
+            th = threading.Thread(target=lambda: out.extend(srv.submit_many(rq[:3])))
+            th.start()
+            th.join()
+            for t in out:
+                srv.wait(t, 60)
+            assert srv.breakdown()["direct_requests"] == 3
+        assert all(v >= 0 for v in info["p99_s"].values())
+        srv.close()
+    for i, (seq, off) in enumerate(reqs):
+        db, dh = _direct(f, seq, off)
+        for name in results:
+            if i < len(results[name]):
+                hits, bits = results[name][i]
+                assert np.array_equal(hits, dh) and np.array_equal(bits, db), (name, i)
+
+
+def test_batch_submission_refuses_all_or_nothing(served):
+    from paper_2606_24417_gb300.sbf import FilterServer, SbfError
+
+    f, _, _, reqs = served
+    srv = FilterServer(f, read_budget_bytes=1 << 20, max_inflight=2)
+    bad_off = reqs[1][1].copy()
+    bad_off[1], bad_off[2] = bad_off[2], bad_off[1]        # offsets decrease
+    with pytest.raises(SbfError) as ei:
+        srv.submit_many([reqs[0], (reqs[1][0], bad_off)])
+    assert ei.value.code == -1
+    assert srv.stats()["completed"] == 0
+    t = srv.submit_many([reqs[0]])
+    hits, _, _ = srv.wait(t[0], 60)
+    assert np.array_equal(hits, _direct(f, *reqs[0])[1])
+    srv.close()
