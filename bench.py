@@ -1193,34 +1193,49 @@ def run_alphabets(args):
         qo = np.concatenate([o1, o2[1:] + o1[-1]]).astype(np.uint64)
         ins_kmers = ref.size // c["sym"] - c["k"] + 1
         q_kmers = (n_s + n_r) * (rlen // c["sym"] - c["k"] + 1)
-        f = SuperBloomFilter(c["k"], c["m"], c["s"], c["H"], c["bits"], shard_bits=512,
-                             canonical=False, alphabet=c["alphabet"])
         dr, dro = dev(ref), dev(np.array([0, ref.size], dtype=np.int64))
         dq, dqo = dev(q), dev(qo.astype(np.int64))
         hits = torch.empty(n_s + n_r, dtype=torch.int32, device="cuda")
+        bits = torch.empty((q.size + 31) // 32, dtype=torch.int32, device="cuda")
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        ti, tq = [], []
-        for rep in range(args.warmup + args.steps):
-            f.clear()
-            ev[0].record()
-            f.insert(dr, dro)
-            ev[1].record()
-            f.query(dq, dqo, hits=hits, want_bits=False)
-            ev[2].record()
-            torch.cuda.synchronize()
-            if rep >= args.warmup:
-                ti.append(ev[0].elapsed_time(ev[1]))
-                tq.append(ev[1].elapsed_time(ev[2]))
-        h = hits.cpu().numpy()
-        out[name] = {"k": c["k"], "m": c["m"], "s": c["s"], "H": c["H"], "filter_bits": c["bits"],
-                     "insert_kmers": ins_kmers, "query_kmers": q_kmers,
-                     "insert_ms": statistics.median(ti), "query_ms": statistics.median(tq),
-                     "insert_kmers_per_s": ins_kmers / (statistics.median(ti) / 1e3),
-                     "query_kmers_per_s": q_kmers / (statistics.median(tq) / 1e3),
-                     "sampled_hit_fraction": float(h[:n_s].sum()) / (n_s * (rlen // c["sym"] - c["k"] + 1)),
-                     "fpr_random": float(h[n_s:].sum()) / (n_r * (rlen // c["sym"] - c["k"] + 1)),
-                     "kernel": "generic" if not f.fused else "fused"}
-        f.close()
+        answers = {}
+        for variant in ("rolling", "generic"):
+            # the generic one-k-mer-per-thread kernels, for comparison
+            if variant == "generic":
+                os.environ["SBF_FORCE_GENERIC"] = "1"
+            f = SuperBloomFilter(c["k"], c["m"], c["s"], c["H"], c["bits"], shard_bits=512,
+                                 canonical=False, alphabet=c["alphabet"])
+            os.environ.pop("SBF_FORCE_GENERIC", None)
+            assert f.kernel_variant == variant
+            ti, tq = [], []
+            for rep in range(args.warmup + args.steps):
+                f.clear()
+                ev[0].record()
+                f.insert(dr, dro)
+                ev[1].record()
+                f.query(dq, dqo, bits=bits, hits=hits)
+                ev[2].record()
+                torch.cuda.synchronize()
+                if rep >= args.warmup:
+                    ti.append(ev[0].elapsed_time(ev[1]))
+                    tq.append(ev[1].elapsed_time(ev[2]))
+            h = hits.cpu().numpy()
+            answers[variant] = (bits.cpu().numpy(), h, f.words())
+            out[f"{name}_{variant}"] = {
+                "k": c["k"], "m": c["m"], "s": c["s"], "H": c["H"], "filter_bits": c["bits"],
+                "insert_kmers": ins_kmers, "query_kmers": q_kmers,
+                "insert_ms": statistics.median(ti), "query_ms": statistics.median(tq),
+                "insert_kmers_per_s": ins_kmers / (statistics.median(ti) / 1e3),
+                "query_kmers_per_s": q_kmers / (statistics.median(tq) / 1e3),
+                "sampled_hit_fraction": float(h[:n_s].sum()) / (n_s * (rlen // c["sym"] - c["k"] + 1)),
+                "fpr_random": float(h[n_s:].sum()) / (n_r * (rlen // c["sym"] - c["k"] + 1)),
+                "kernel": f.kernel_variant}
+            f.close()
+        out[f"{name}_identical"] = all(np.array_equal(a, b) for a, b in
+                                       zip(answers["rolling"], answers["generic"]))
+        out[f"{name}_speedup"] = {
+            "insert": out[f"{name}_generic"]["insert_ms"] / out[f"{name}_rolling"]["insert_ms"],
+            "query": out[f"{name}_generic"]["query_ms"] / out[f"{name}_rolling"]["query_ms"]}
     print(json.dumps({"workload": "alphabets: protein filter on a 100M-residue synthetic proteome "
                       "(150-residue peptides) and DNA-triplet filter on the 100 Mbp genome "
                       "(450 bp reads); 1M sampled (1% substitutions) + 1M random queries each",

@@ -133,9 +133,13 @@ uint64_t sbf_num_words(const sbf_filter* f);
  * [x*W, (x+1)*W), W = shard_bits / 64).  Owned by the filter. */
 const uint64_t* sbf_device_words(const sbf_filter* f);
 
-/* Which kernels serve this filter: 1 = the fused kernels (compiled grid
- * w = k-m+1 in {12, 16, 18, 20}, H in {1, 2, 4, 8}), 0 = the generic
- * one-k-mer-per-thread kernels.  Both give identical bits. */
+/* Which kernels serve this filter: 1 = the fused kernels (DNA, compiled grid
+ * w = k-m+1 in {12, 16, 18, 20}, H in {1, 2, 4, 8}); 2 = the rolling kernels
+ * (every other parameter set and alphabet: one thread per 32 start
+ * positions, a rolling k-mer, s-mers shared by the k-mers of a run of one
+ * shard); 0 = the generic one-k-mer-per-thread kernels, used only when the
+ * environment variable SBF_FORCE_GENERIC is set at sbf_create (a second,
+ * independent path for tests).  All give identical bits. */
 int sbf_kernel_variant(const sbf_filter* f);
 
 /* Device status of the filter's kernels: *status = 0 while every launch ran

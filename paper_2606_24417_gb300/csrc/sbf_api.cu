@@ -80,16 +80,19 @@ int check_params(int k, int m, int s, int H, uint64_t bits, int shard_bits) {
 
 int launch_insert(sbf_filter* f, const uint8_t* seq, uint64_t seq_len, const uint64_t* off,
                   uint64_t n_reads, cudaStream_t st) {
-  cudaError_t e = f->fused ? fused_insert(f->geom, seq, seq_len, off, n_reads, st)
-                           : generic_insert(f->geom, seq, seq_len, off, n_reads, st);
+  cudaError_t e = f->variant == 1 ? fused_insert(f->geom, seq, seq_len, off, n_reads, st)
+                 : f->variant == 2 ? rolling_insert(f->geom, seq, seq_len, off, n_reads, st)
+                                   : generic_insert(f->geom, seq, seq_len, off, n_reads, st);
   return e == cudaSuccess ? SBF_OK : cuda_fail(e, "insert launch");
 }
 
 int launch_query(const sbf_filter* f, const uint8_t* seq, uint64_t seq_len, const uint64_t* off,
                  uint64_t n_reads, uint32_t* bits, uint32_t* hits, uint64_t* stats,
                  cudaStream_t st) {
-  cudaError_t e = f->fused ? fused_query(f->geom, seq, seq_len, off, n_reads, bits, hits, stats, st)
-                           : generic_query(f->geom, seq, seq_len, off, n_reads, bits, hits, stats, st);
+  cudaError_t e =
+      f->variant == 1 ? fused_query(f->geom, seq, seq_len, off, n_reads, bits, hits, stats, st)
+      : f->variant == 2 ? rolling_query(f->geom, seq, seq_len, off, n_reads, bits, hits, stats, st)
+                        : generic_query(f->geom, seq, seq_len, off, n_reads, bits, hits, stats, st);
   return e == cudaSuccess ? SBF_OK : cuda_fail(e, "query launch");
 }
 
@@ -163,6 +166,7 @@ int sbf_create_full(int k, int m, int s, int H, uint64_t bits, int shard_bits, i
   f->geom.status = status;
   f->n_words = n_words;
   f->fused = fused_supported(f->geom);
+  f->variant = f->fused ? 1 : getenv("SBF_FORCE_GENERIC") ? 0 : 2;
   *out = f;
   return SBF_OK;
 }
@@ -230,7 +234,7 @@ int sbf_device_status(const sbf_filter* f, uint32_t* status, int clear) {
   return e == cudaSuccess ? SBF_OK : cuda_fail(e, "device_status");
 }
 
-int sbf_kernel_variant(const sbf_filter* f) { return f && f->fused ? 1 : 0; }
+int sbf_kernel_variant(const sbf_filter* f) { return f ? f->variant : 0; }
 
 const uint64_t* sbf_device_words(const sbf_filter* f) { return f ? f->geom.words : nullptr; }
 

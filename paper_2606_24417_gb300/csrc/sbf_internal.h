@@ -15,6 +15,9 @@ struct sbf_filter {
   int device = 0;
   uint64_t n_words = 0;
   bool fused = false;  // a specialised kernel exists for these parameters
+  // kernels that serve the filter: 1 fused, 2 rolling (every other parameter
+  // set), 0 generic one-k-mer-per-thread (only when SBF_FORCE_GENERIC is set)
+  int variant = 0;
   // host-input path (sbf_*_host): reusable device buffers and two streams
   std::mutex host_mu;
   cudaStream_t host_streams[2] = {nullptr, nullptr};
@@ -46,6 +49,13 @@ void clear_error();
 cudaError_t generic_insert(const Geom& g, const uint8_t* seq, uint64_t seq_len,
                            const uint64_t* off, uint64_t n_reads, cudaStream_t st);
 cudaError_t generic_query(const Geom& g, const uint8_t* seq, uint64_t seq_len,
+                          const uint64_t* off, uint64_t n_reads, uint32_t* bits, uint32_t* hits,
+                          uint64_t* stats, cudaStream_t st);
+
+// Rolling kernels: any valid parameter set, one thread per 32 start positions.
+cudaError_t rolling_insert(const Geom& g, const uint8_t* seq, uint64_t seq_len,
+                           const uint64_t* off, uint64_t n_reads, cudaStream_t st);
+cudaError_t rolling_query(const Geom& g, const uint8_t* seq, uint64_t seq_len,
                           const uint64_t* off, uint64_t n_reads, uint32_t* bits, uint32_t* hits,
                           uint64_t* stats, cudaStream_t st);
 

@@ -194,8 +194,15 @@ class SuperBloomFilter:
 
     @property
     def fused(self) -> bool:
-        """True if the fused kernels serve this filter (else the generic ones)."""
-        return bool(self._lib.sbf_kernel_variant(self._h))
+        """True if the fused kernels serve this filter."""
+        return self._lib.sbf_kernel_variant(self._h) == 1
+
+    @property
+    def kernel_variant(self) -> str:
+        """The kernels that serve this filter: 'fused', 'rolling' (every
+        parameter set outside the fused grid) or 'generic' (one k-mer per
+        thread, only when the environment sets SBF_FORCE_GENERIC)."""
+        return {0: "generic", 1: "fused", 2: "rolling"}[self._lib.sbf_kernel_variant(self._h)]
 
     def device_status(self, clear: bool = False) -> int:
         """0 while every launch on this filter ran to completion; bit 0 set

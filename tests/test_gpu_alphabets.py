@@ -138,3 +138,56 @@ def test_protein_fasta_input(tmp_path):
     t = SuperBloomFilter(10, 5, 8, 4, 1 << 20, canonical=False, alphabet="dna_triplet")
     with pytest.raises(ValueError):
         insert_fastx(t, str(tmp_path / "p.fa"))
+
+
+ROLLING_CASES = [
+    # k, m, s, H, bits, B, canonical, layout, alphabet
+    (12, 6, 10, 4, 1 << 24, 512, False, 0, 1),
+    (10, 5, 8, 4, 1 << 23, 512, False, 0, 2),
+    (31, 16, 28, 16, 1 << 24, 512, True, 0, 0),    # DNA outside the fused grid (H = 16)
+    (25, 11, 21, 3, 1 << 24, 256, True, 0, 0),     # w = 15, H = 3
+    (31, 16, 28, 12, 1 << 24, 256, False, 1, 0),   # the paper's layout, salted multiply
+]
+
+
+@pytest.mark.parametrize("case", ROLLING_CASES, ids=lambda c: "_".join(map(str, c)))
+def test_rolling_kernels_equal_generic_and_oracle(case, monkeypatch):
+    """Every filter outside the fused grid runs the rolling kernels; on a
+    larger workload (whole genome inserted, 200,000 ragged reads, junk bytes)
+    their words, answer bits, hits and run statistics equal the generic
+    one-k-mer-per-thread kernels' and, on a sample, the oracle's."""
+    from paper_2606_24417_gb300.sbf import SuperBloomFilter
+
+    k, m, s, H, bits, B, canon, layout, alphabet = case
+    if alphabet == 1:
+        src = synth.protein_sequence(5_000_000, 41)
+        q, q_off = ragged(src, 200_000, 43)
+        junk = b"*-X.1"
+    else:
+        src = synth.bacterial_genome(5_000_000, seed=41)
+        q, q_off = ragged(src, 200_000, 43, junk=b"N")
+        junk = b"N"
+    ins, ins_off = ragged(src, 20_000, 42, junk=junk)
+    kw = dict(shard_bits=B, canonical=canon, layout=layout, alphabet=alphabet)
+    fr = SuperBloomFilter(k, m, s, H, bits, **kw)
+    monkeypatch.setenv("SBF_FORCE_GENERIC", "1")
+    fg = SuperBloomFilter(k, m, s, H, bits, **kw)
+    monkeypatch.delenv("SBF_FORCE_GENERIC")
+    assert fr.kernel_variant == "rolling" and fg.kernel_variant == "generic"
+    for f in (fr, fg):
+        f.insert(dev(ins), dev_off(ins_off))
+    assert np.array_equal(fr.words(), fg.words())
+    out = []
+    for f in (fr, fg):
+        st = torch.zeros(3, dtype=torch.int64, device="cuda")
+        b_, h_ = f.query(dev(q), dev_off(q_off), stats=st)
+        out.append((b_.cpu().numpy(), h_.cpu().numpy(), st.cpu().tolist()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2] and out[0][2][2] > 0
+    o = OracleSBF(k, m, s, H, bits, **kw)
+    o.set_words(fr.words())
+    n = 3000
+    ob, oh = o.query(q[:int(q_off[n])], q_off[:n + 1])
+    assert np.array_equal(out[0][1].view(np.uint32)[:n], oh)
+    got = np.unpackbits(out[0][0].view(np.uint8), bitorder="little")[:int(q_off[n])]
+    assert np.array_equal(got, np.unpackbits(ob.view(np.uint8), bitorder="little")[:int(q_off[n])])
