@@ -47,6 +47,14 @@ constexpr int kLanePos = 16;        // start positions per lane
 constexpr int kWarps = 4;           // warps per block
 constexpr int kThreads = 32 * kWarps;
 constexpr int kSlotCap = 64;        // runs per iteration with a shard copy in shared memory
+// Windows of 12 or less (m = 20 at k = 31) give about 2/(w+1) * 496 = 76 runs
+// per iteration, more than 64 slots, and an insert's runs past the last slot
+// set their bits with global atomics.  Inserts with such windows keep 96
+// slots in shared memory (m = 20, H = 8 inserts 3.6x faster on 512-bit shards,
+// 2.3x on 256-bit); queries keep 64, because their fallback is a plain load
+// and the larger array costs the 512-bit-shard kernels a resident block.
+template <int W, bool INSERT>
+constexpr int slot_cap() { return (INSERT && W <= 12) ? 96 : kSlotCap; }
 constexpr int kStage = 34;          // staged 16-base words per iteration (544 bases)
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
@@ -225,7 +233,7 @@ struct Params {
   uint32_t big;           // a segment's filter has kTmaMinBytes or more (query: BULK kernels)
 };
 
-template <int H, int B, bool KEY64>
+template <int SC, int H, int B, bool KEY64>
 struct alignas(16) WarpSmem {
   using L = Layout<H, B>;
   using Pack = typename L::Pack;
@@ -233,7 +241,7 @@ struct alignas(16) WarpSmem {
   // the 32-bit form needs fewer than 2^32 shards)
   using SlotT = typename std::conditional<KEY64, uint64_t, uint32_t>::type;
   static constexpr int kHsStride = sizeof(Pack) == 4 ? 34 : 33;  // bank-conflict-free transposes
-  uint32_t shard[kSlotCap * L::SLOT];    // shard copies (query) or masks (insert)
+  uint32_t shard[SC * L::SLOT];          // shard copies (query) or masks (insert)
   SlotT slot_x[512];
   Pack hs[kLanePos * kHsStride];         // s-mer bit-address packs, [j][lane]
   uint16_t end_slot[512];                // slot of each run end
@@ -371,7 +379,8 @@ __device__ bool prev_kmer_key(const Geom& g, const uint8_t* seq, uint64_t seq_le
 // wait for shard copies ran out (the filter's status word is set).  BULK:
 // the kernel variant for launches with a filter of kTmaMinBytes or more.
 template <int W, int H, int B, bool KEY64, bool INSERT, bool BULK>
-__device__ __forceinline__ bool run_range(WarpSmem<H, B, KEY64>& S, const Params& P,
+__device__ __forceinline__ bool run_range(WarpSmem<slot_cap<W, INSERT>(), H, B, KEY64>& S,
+                                          const Params& P,
                                           const Segment& seg, uint64_t it0, uint64_t it1,
                                           int lane, unsigned long long& st_valid,
                                           unsigned long long& st_runs,
@@ -379,10 +388,11 @@ __device__ __forceinline__ bool run_range(WarpSmem<H, B, KEY64>& S, const Params
   using L = Layout<H, B>;
   using Pack = typename L::Pack;
   using KeyT = typename std::conditional<KEY64, uint64_t, uint32_t>::type;
-  using Sm = WarpSmem<H, B, KEY64>;
+  using Sm = WarpSmem<slot_cap<W, INSERT>(), H, B, KEY64>;
   constexpr int U = Shape<W>::kUseful;
   constexpr int ADV = Shape<W>::kAdvance;
   constexpr int HS = Sm::kHsStride;
+  constexpr int SC = slot_cap<W, INSERT>();  // runs of an iteration with a slot in shared memory
   Geom g = P.g;
   g.words = seg.words;
   g.n_shards = seg.n_shards;
@@ -689,8 +699,8 @@ __device__ __forceinline__ bool run_range(WarpSmem<H, B, KEY64>& S, const Params
     // ---------------- shards of the runs: index, then async copy ----------
     const uint64_t n_shards = g.n_shards;
     const bool masked = g.layout == 1;  // the paper's shard rule: key & (2^P - 1)
-    // slots [kTmaFromSlot, min(total, kSlotCap)) of a large filter go to the TMA engine
-    const uint32_t n_copy = total_slots < (uint32_t)kSlotCap ? total_slots : (uint32_t)kSlotCap;
+    // slots [kTmaFromSlot, min(total, SC)) of a large filter go to the TMA engine
+    const uint32_t n_copy = total_slots < (uint32_t)SC ? total_slots : (uint32_t)SC;
     uint32_t n_bulk = 0;
     if constexpr (BULK)
       n_bulk = (n_shards * (uint64_t)(B / 8) >= kTmaMinBytes && n_copy > kTmaFromSlot)
@@ -718,7 +728,7 @@ __device__ __forceinline__ bool run_range(WarpSmem<H, B, KEY64>& S, const Params
         x = __umul64hi(mix64(mu ^ kShardKey), n_shards);
       }
       S.slot_x[si] = (typename Sm::SlotT)x;
-      if (si < (uint32_t)kSlotCap) {
+      if (si < (uint32_t)SC) {
         if constexpr (INSERT) {
 #pragma unroll
           for (int w = 0; w < L::W32; w += 4)
@@ -749,7 +759,9 @@ __device__ __forceinline__ bool run_range(WarpSmem<H, B, KEY64>& S, const Params
     constexpr uint64_t K30 = kSmerKey ^ (kSmerKey >> 30);
     const uint32_t sh_s = 64u - 2u * (uint32_t)s;
     const uint32_t smask_hi = (uint32_t)(smask >> 32);
-    constexpr int kHashUnroll = KEY64 ? kLanePos : 4;  // small code where registers allow
+    // four positions per step: with 64-bit order keys a fully unrolled loop
+    // made inserts 6-8% and queries 3-6% slower (code size)
+    constexpr int kHashUnroll = 4;
 #pragma unroll kHashUnroll
     for (int j = 0; j < kLanePos; ++j) {
       const uint32_t hi = __funnelshift_l(F1, F0, 2 * j);
@@ -781,7 +793,7 @@ __device__ __forceinline__ bool run_range(WarpSmem<H, B, KEY64>& S, const Params
 
     // ---------------- pair tests / sets ------------------------------------
     auto test_pair = [&](Pack pk, uint32_t slot) -> bool {
-      if (slot < (uint32_t)kSlotCap) return test_slot<H, B>(&S.shard[slot * L::SLOT], pk) != 0u;
+      if (slot < (uint32_t)SC) return test_slot<H, B>(&S.shard[slot * L::SLOT], pk) != 0u;
       uint32_t acc = 1u;
       const uint32_t* gp = words32 + S.slot_x[slot] * (uint64_t)L::W32;
 #pragma unroll
@@ -793,7 +805,7 @@ __device__ __forceinline__ bool run_range(WarpSmem<H, B, KEY64>& S, const Params
       return acc & 1u;
     };
     auto set_pair = [&](Pack pk, uint32_t slot) {
-      if (slot < (uint32_t)kSlotCap) {
+      if (slot < (uint32_t)SC) {
         set_slot<H, B>(&S.shard[slot * L::SLOT], pk);
       } else {
         uint32_t* gp = words32 + S.slot_x[slot] * (uint64_t)L::W32;
@@ -876,7 +888,7 @@ __device__ __forceinline__ bool run_range(WarpSmem<H, B, KEY64>& S, const Params
 
     if constexpr (INSERT) {
       // ---------------- flush run masks: coalesced 64-bit atomics ----------
-      const uint32_t n_mem = total_slots < (uint32_t)kSlotCap ? total_slots : (uint32_t)kSlotCap;
+      const uint32_t n_mem = total_slots < (uint32_t)SC ? total_slots : (uint32_t)SC;
       constexpr uint32_t W64 = B / 64;
       const uint32_t n_words = n_mem * W64;
       for (uint32_t i = lane; i < n_words; i += 32) {
@@ -1005,7 +1017,7 @@ constexpr int min_blocks() {
 template <int W, int H, int B, bool KEY64, bool INSERT, bool BULK>
 __global__ void __launch_bounds__(kThreads, min_blocks<KEY64, INSERT, B>()) fused_kernel(Params P) {
   static_assert(!(INSERT && BULK), "bulk shard copies are a query variant");
-  using Sm = WarpSmem<H, B, KEY64>;
+  using Sm = WarpSmem<slot_cap<W, INSERT>(), H, B, KEY64>;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   Sm& S = reinterpret_cast<Sm*>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
@@ -1092,7 +1104,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<KEY64, INSERT, B>()) fuse
 template <int W, int H, int B, bool KEY64, bool INSERT, bool BULK = false>
 cudaError_t launch(const Params& P, cudaStream_t st) {
   auto kern = fused_kernel<W, H, B, KEY64, INSERT, BULK>;
-  constexpr size_t smem = sizeof(WarpSmem<H, B, KEY64>) * kWarps;
+  constexpr size_t smem = sizeof(WarpSmem<slot_cap<W, INSERT>(), H, B, KEY64>) * kWarps;
   static int blocks_per_sm = 0;  // per instantiation; same on every GB300
   if (blocks_per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
