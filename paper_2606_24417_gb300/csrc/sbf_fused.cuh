@@ -190,18 +190,32 @@ __device__ __forceinline__ uint32_t test_slot(const uint32_t* slot_words,
   return acc & 1u;
 }
 
+// Insert: the H bits, hash (ii + rot) mod H at step ii, so that lanes of one
+// run (consecutive lanes, rot = lane mod H) set bits in different sectors at
+// the same time instead of queueing on the same shared words.
 template <int H, int B>
-__device__ __forceinline__ void set_slot(uint32_t* slot_words, typename Layout<H, B>::Pack pk) {
+__device__ __forceinline__ void set_slot_rot(uint32_t* slot_words, typename Layout<H, B>::Pack pk,
+                                             uint32_t rot) {
   using L = Layout<H, B>;
   constexpr uint32_t SBY = L::SB / 8;
   constexpr uint32_t OM = (SBY - 1u) & ~3u;
   char* base = reinterpret_cast<char*>(slot_words);
 #pragma unroll
-  for (int i = 0; i < H; ++i) {
-    const uint32_t p = pack_addr<H, B>(pk, i);
-    atomicOr(reinterpret_cast<uint32_t*>(base + (i % L::S) * SBY + ((p >> 3) & OM)), 1u << (p & 31u));
+  for (int ii = 0; ii < H; ++ii) {
+    const uint32_t i = ((uint32_t)ii + rot) & (uint32_t)(H - 1);
+    uint32_t p;
+    if constexpr (H == 1) {
+      p = (uint32_t)pk;   // one address of up to 9 bits, not a byte
+    } else if constexpr (H == 8) {
+      p = (uint32_t)(pk >> (8 * i)) & 0xFFu;
+    } else {
+      p = ((uint32_t)pk >> (8 * i)) & 0xFFu;
+    }
+    atomicOr(reinterpret_cast<uint32_t*>(base + (i & (uint32_t)(L::S - 1)) * SBY + ((p >> 3) & OM)),
+             1u << (p & 31u));
   }
 }
+
 
 // One share of a launch: a filter, the bytes and reads it serves and where
 // its answers go.  Positions are relative to `seq`; the offsets use the same
@@ -806,7 +820,7 @@ __device__ __forceinline__ bool run_range(WarpSmem<slot_cap<W, INSERT>(), H, B, 
     };
     auto set_pair = [&](Pack pk, uint32_t slot) {
       if (slot < (uint32_t)SC) {
-        set_slot<H, B>(&S.shard[slot * L::SLOT], pk);
+        set_slot_rot<H, B>(&S.shard[slot * L::SLOT], pk, (uint32_t)lane & (uint32_t)(H - 1));
       } else {
         uint32_t* gp = words32 + S.slot_x[slot] * (uint64_t)L::W32;
 #pragma unroll

@@ -7,7 +7,10 @@
 // word).  It finds the read of its first position once, then walks the
 // chunk's reads with a rolling k-mer: each symbol is decoded once and
 // shifted in (Sec. IV-C packing, first symbol most significant), instead of
-// re-packing k symbols and re-searching the read table per k-mer.
+// re-packing k symbols and re-searching the read table per k-mer.  The
+// minimizer slides too: a full scan of the k - m + 1 windows only when the
+// window holding the smallest key leaves the k-mer (about every (w+1)/2
+// positions on random sequence), one new window otherwise.
 //
 // Consecutive valid k-mers of one read with the same shard share their
 // s-mers' tests: k-mer j needs s-mers j..j+z (z = k - s) in shard(j), so
@@ -116,6 +119,7 @@ __global__ void __launch_bounds__(kThreads) rolling_kernel(Geom g, const uint8_t
   const int z = g.k - g.s;
   const uint64_t kmask = bit_mask(g.k * g.sym_bits);
   const uint64_t span = (uint64_t)g.k * sb;  // bytes of one k-mer
+  const int n_win = g.k - g.m + 1;           // m-mer windows of a k-mer
   unsigned long long n_valid = 0, n_runs = 0, n_pos = 0;
   // query: each thread's copy of its current run's shard (up to 8 words),
   // word-major so that a warp's accesses to one word index are conflict-free;
@@ -157,6 +161,12 @@ __global__ void __launch_bounds__(kThreads) rolling_kernel(Geom g, const uint8_t
         uint64_t run_x = 0, next_t = 0, last_fail = 0, prev_mu = 0;
         bool has_fail = false;
         bool prev_valid = false; // the previous position's k-mer was valid (same read)
+        // sliding minimum of the previous position's k-mer: smallest order key,
+        // its m-mer and its window index (keys are a bijection of m-mers, so
+        // equal keys are equal m-mers)
+        bool have_min = false;
+        uint64_t min_key = 0, min_val = 0;
+        int min_pos = 0;
         if (!INSERT && stats && p >= rs + sb)     // run heads across the chunk edge
           prev_valid = kmer_min_at(g, seq, rs, re, p - sb, prev_mu);
         for (; p < p_end && p + span <= re; p += sb, q += sb) {
@@ -171,9 +181,34 @@ __global__ void __launch_bounds__(kThreads) rolling_kernel(Geom g, const uint8_t
           if (good < g.k) {
             prev_valid = false;
             in_run = false;
+            have_min = false;
             continue;
           }
-          const uint64_t mu = min_of(g, fwd, rc);
+          // the minimizer slides with the k-mer: while the window holding the
+          // smallest key stays inside, only the new last window is compared;
+          // when it leaves, all k - m + 1 windows are scanned again
+          if (have_min && min_pos > 0) {
+            const uint64_t v = sub_value(g, fwd, rc, n_win - 1, g.m);
+            const uint64_t key = order_key(v, g.m * g.sym_bits);
+            --min_pos;
+            if (key < min_key) {
+              min_key = key;
+              min_val = v;
+              min_pos = n_win - 1;
+            }
+          } else {
+            for (int i = 0; i < n_win; ++i) {
+              const uint64_t v = sub_value(g, fwd, rc, i, g.m);
+              const uint64_t key = order_key(v, g.m * g.sym_bits);
+              if (i == 0 || key < min_key) {
+                min_key = key;
+                min_val = v;
+                min_pos = i;
+              }
+            }
+            have_min = true;
+          }
+          const uint64_t mu = min_val;
           const uint64_t x = shard_of(g, mu);
           if (!INSERT && stats) {
             ++n_valid;
