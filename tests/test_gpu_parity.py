@@ -222,6 +222,16 @@ def test_host_path_matches_device(monkeypatch, params):
     ph = torch.empty(hh.size, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
     f.query_host(q_seq, q_off, bits=pb, hits=ph)
     assert np.array_equal(pb, ob) and np.array_equal(ph, oh)
+    # pinned inputs: the fused kernels read them in place over the link
+    # instead of copying chunks in; same answers, same filter
+    pq = torch.from_numpy(q_seq).pin_memory().numpy()
+    po = torch.from_numpy(q_off.view(np.int64)).pin_memory().numpy().view(np.uint64)
+    f.query_host(pq, po, bits=pb, hits=ph)
+    assert np.array_equal(pb, ob) and np.array_equal(ph, oh)
+    f2 = make_filter(*params[:5], params[5], params[6])
+    f2.insert_host(torch.from_numpy(ins_seq).pin_memory().numpy(),
+                   torch.from_numpy(ins_off.view(np.int64)).pin_memory().numpy().view(np.uint64))
+    assert np.array_equal(f2.words(), o.words())
     monkeypatch.delenv("SBF_HOST_CHUNK_BYTES")
     hb2, hh2 = f.query_host(q_seq, q_off)
     assert np.array_equal(hb2, ob) and np.array_equal(hh2, oh)
