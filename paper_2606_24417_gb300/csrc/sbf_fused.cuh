@@ -407,6 +407,11 @@ __device__ __forceinline__ bool run_range(WarpSmem<slot_cap<W, INSERT>(), H, B, 
   constexpr int ADV = Shape<W>::kAdvance;
   constexpr int HS = Sm::kHsStride;
   constexpr int SC = slot_cap<W, INSERT>();  // runs of an iteration with a slot in shared memory
+  // Queries test own pairs without masks or a global fallback when all runs of
+  // an iteration have a slot.  That pays where the runs (about 2/(W+1) of
+  // the 496 positions) usually fit the 64 slots, W >= 16; at W = 12 they
+  // average 76, and the second loop only adds code (2-5% slower there).
+  constexpr bool kFastOwn = !INSERT && W > 12;
   Geom g = P.g;
   g.words = seg.words;
   g.n_shards = seg.n_shards;
@@ -691,7 +696,7 @@ __device__ __forceinline__ bool run_range(WarpSmem<slot_cap<W, INSERT>(), H, B, 
           S.slot_x[sl] = (typename Sm::SlotT)mk[j];
           S.slot_head[sl] = (uint16_t)t;
         }
-        if ((valid16 >> j) & 1u) S.slot_of[j * 34 + lane] = (uint16_t)sl;
+        if (kFastOwn || ((valid16 >> j) & 1u)) S.slot_of[j * 34 + lane] = (uint16_t)sl;
         if ((end16 >> j) & 1u) {
           S.end_list[en] = (uint16_t)t;
           S.end_slot[en] = (uint16_t)sl;
@@ -834,9 +839,50 @@ __device__ __forceinline__ bool run_range(WarpSmem<slot_cap<W, INSERT>(), H, B, 
     // own pairs (t, shard(t)), position-per-lane: t = 32*pass + lane, so
     // t & 15 = lane & 15 and t >> 4 = 2*pass + (lane >> 4); lanes of one pass
     // mostly share a few run slots, so their shard reads broadcast.  Two
-    // passes per step for independent work; invalid positions test slot 0
-    // (their slot entry may be stale) and are masked out.
-    {
+    // passes per step for independent work.
+    if constexpr (kFastOwn) {
+      // Own bits of invalid positions are never read: the AND below takes
+      // position t + d only while t + d is in t's run (all valid), and the
+      // answer word keeps valid positions only.  So no lane masks its test.
+      const uint32_t hs_i0 = (lane & 15u) * HS + (lane >> 4);
+      const uint32_t so_i0 = (lane & 15u) * 34 + (lane >> 4);
+      if (total_slots <= (uint32_t)SC) {
+        // every run has a shared copy; an invalid position's slot entry
+        // (written, but of no run) is reduced into range
+        static_assert((SC & (SC - 1)) == 0, "query slot count is a power of two");
+#pragma unroll 4
+        for (int pass = 0; pass < 16; pass += 2) {
+          const uint32_t sla = S.slot_of[so_i0 + 2 * pass] & (uint32_t)(SC - 1);
+          const uint32_t slb = S.slot_of[so_i0 + 2 * pass + 2] & (uint32_t)(SC - 1);
+          const unsigned own_a = __ballot_sync(
+              kFull, test_slot<H, B>(&S.shard[sla * L::SLOT], S.hs[hs_i0 + 2 * pass]) != 0u);
+          const unsigned own_b = __ballot_sync(
+              kFull, test_slot<H, B>(&S.shard[slb * L::SLOT], S.hs[hs_i0 + 2 * pass + 2]) != 0u);
+          if (lane == 0) {
+            S.own_w[pass] = own_a;
+            S.own_w[pass + 1] = own_b;
+          }
+        }
+      } else {
+        // some runs test against global memory: invalid positions test slot
+        // 0, since their entry may index past the runs
+#pragma unroll 2
+        for (int pass = 0; pass < 16; pass += 2) {
+          const uint32_t va = (S.valid_w[pass] >> lane) & 1u;
+          const uint32_t vb = (S.valid_w[pass + 1] >> lane) & 1u;
+          const uint32_t sla = va ? (uint32_t)S.slot_of[so_i0 + 2 * pass] : 0u;
+          const uint32_t slb = vb ? (uint32_t)S.slot_of[so_i0 + 2 * pass + 2] : 0u;
+          const unsigned own_a = __ballot_sync(kFull, test_pair(S.hs[hs_i0 + 2 * pass], sla));
+          const unsigned own_b = __ballot_sync(kFull, test_pair(S.hs[hs_i0 + 2 * pass + 2], slb));
+          if (lane == 0) {
+            S.own_w[pass] = own_a;
+            S.own_w[pass + 1] = own_b;
+          }
+        }
+      }
+    } else {
+      // invalid positions test slot 0 (their slot entry may be stale) and
+      // are masked out
       const uint32_t hs_i0 = (lane & 15u) * HS + (lane >> 4);
       const uint32_t so_i0 = (lane & 15u) * 34 + (lane >> 4);
 #pragma unroll 2
