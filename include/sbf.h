@@ -277,8 +277,8 @@ int sbf_batch_tune(sbf_batch* b, int insert, const uint8_t* d_seq, uint64_t seq_
  * reaches the array in the parameters of small kernels (32 entries each), so
  * the call does not wait on the host for earlier work on its stream.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls on a device share the array and each call
+ * (cudaGetSymbolAddress) with that device current.  All calls on a device
+ * share the array and each call
  * resets what it needs, so calls whose work overlaps on the GPU (other
  * streams, other host threads without ordering) race: order them. */
 int sbf_batch_query_noalloc(sbf_filter* const* filters, int n_filters, const uint8_t* d_seq,
