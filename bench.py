@@ -568,7 +568,8 @@ def run_ours(args, rank, world, local_rank):
         "alu": alu,
         "e2e": {"value": e2e_value, "unit": "k-mers/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "answers_match_device": same},
-        "gpu_launches": 2 * args.steps,
+        # per step: the insert kernel, the query kernel and its short-read hit pass
+        "gpu_launches": 3 * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,
         "filter_sizes": sizes,

@@ -43,6 +43,7 @@ struct sbf_batch {
     int insert;
     const void* seq;
     uint64_t seq_len;
+    const void* off;  // the short-read hit pass reads the offsets
     void* bits;
     void* hits;
     uint64_t n_reads;
@@ -51,7 +52,7 @@ struct sbf_batch {
     int dynamic;
     uint32_t chunk, grid_blocks;
     bool operator==(const Key& o) const {
-      return insert == o.insert && seq == o.seq && seq_len == o.seq_len && bits == o.bits &&
+      return insert == o.insert && seq == o.seq && seq_len == o.seq_len && off == o.off && bits == o.bits &&
              hits == o.hits && n_reads == o.n_reads && n_segs == o.n_segs && iters == o.iters &&
              dynamic == o.dynamic && chunk == o.chunk && grid_blocks == o.grid_blocks;
     }
@@ -159,8 +160,8 @@ int upload_table(sbf_batch* b, const std::vector<Segment>& t, cudaStream_t st) {
 
 // Memsets of the outputs (query) and of the work counter, then the launch.
 cudaError_t enqueue_fused(sbf_batch* b, bool insert, const uint8_t* seq, uint64_t seq_len,
-                          uint64_t n_reads, uint32_t* bits, uint32_t* hits, uint32_t n_segs,
-                          uint64_t iters, cudaStream_t st) {
+                          const uint64_t* off, uint64_t n_reads, uint32_t* bits, uint32_t* hits,
+                          uint32_t n_segs, uint64_t iters, cudaStream_t st) {
   cudaError_t e;
   if (!insert) {
     if (bits && seq_len && (e = cudaMemsetAsync(bits, 0, ((seq_len + 31) / 32) * 4, st)) != cudaSuccess)
@@ -180,7 +181,11 @@ cudaError_t enqueue_fused(sbf_batch* b, bool insert, const uint8_t* seq, uint64_
   P.chunk = sc.chunk > 0 ? sc.chunk : 1;
   P.grid_blocks = sc.grid_blocks;
   P.big = b->big ? 1u : 0u;
-  return sbf::fused::launch_params(P, insert, st);
+  // every segment's answers and hits sit in the one pair of output arrays,
+  // indexed by position and read: one short-read pass covers all filters
+  P.hits_above = sbf::fused::hits_above_for(seq_len, !insert && bits && hits && iters);
+  if ((e = sbf::fused::launch_params(P, insert, st)) != cudaSuccess) return e;
+  return sbf::fused::short_read_hits(bits, off, n_reads, seq_len, P.hits_above, hits, st);
 }
 
 int run_batch(sbf_batch* b, bool insert, const uint8_t* d_seq, uint64_t seq_len, const uint64_t* d_off,
@@ -227,7 +232,7 @@ int run_batch(sbf_batch* b, bool insert, const uint8_t* d_seq, uint64_t seq_len,
   if (rc != SBF_OK) return rc;
   const uint32_t n_segs = (uint32_t)table.size();
   if (mode == SBF_BATCH_FUSED)
-    return (e = enqueue_fused(b, insert, d_seq, seq_len, n_reads, d_bits, d_hits, n_segs, iters, st)) ==
+    return (e = enqueue_fused(b, insert, d_seq, seq_len, d_off, n_reads, d_bits, d_hits, n_segs, iters, st)) ==
                    cudaSuccess
                ? SBF_OK
                : cuda_fail(e, "batched launch");
@@ -236,6 +241,7 @@ int run_batch(sbf_batch* b, bool insert, const uint8_t* d_seq, uint64_t seq_len,
   key.insert = insert ? 1 : 0;
   key.seq = d_seq;
   key.seq_len = seq_len;
+  key.off = insert ? nullptr : d_off;
   key.bits = insert ? nullptr : d_bits;
   key.hits = insert ? nullptr : d_hits;
   key.n_reads = n_reads;
@@ -250,13 +256,13 @@ int run_batch(sbf_batch* b, bool insert, const uint8_t* d_seq, uint64_t seq_len,
       b->graph = nullptr;
     }
     // one eager launch initialises the kernel attributes outside the capture
-    if ((e = enqueue_fused(b, insert, d_seq, seq_len, n_reads, d_bits, d_hits, n_segs, 0, st)) != cudaSuccess)
+    if ((e = enqueue_fused(b, insert, d_seq, seq_len, d_off, n_reads, d_bits, d_hits, n_segs, 0, st)) != cudaSuccess)
       return cuda_fail(e, "kernel setup");
     cudaGraph_t g = nullptr;
     cudaStream_t cs = b->capture_stream;
     if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
       return cuda_fail(e, "begin capture");
-    cudaError_t le = enqueue_fused(b, insert, d_seq, seq_len, n_reads, d_bits, d_hits, n_segs, iters, cs);
+    cudaError_t le = enqueue_fused(b, insert, d_seq, seq_len, d_off, n_reads, d_bits, d_hits, n_segs, iters, cs);
     e = cudaStreamEndCapture(cs, &g);
     if (le != cudaSuccess || e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);

@@ -4,6 +4,8 @@
 // set runs the generic kernels with identical results.
 #include "sbf_fused.cuh"
 
+#include <cstdlib>
+
 namespace sbf {
 namespace fused {
 cudaError_t run_w12(const Params&, int, int, bool, cudaStream_t);
@@ -51,6 +53,50 @@ static Params single(const Geom& g, const uint8_t* seq, uint64_t seq_len, const 
 
 cudaError_t launch_params(const Params& P, bool insert, cudaStream_t st) { return run(P, insert, st); }
 
+// Hits of the reads of at most `above` positions, one thread per read: the
+// set answer bits at the read's start positions [min(off[r], seq_len),
+// min(off[r+1], seq_len)) -- the k-mers of read r that Alg. 2 reports present.
+// The query kernel counted the longer reads itself and left these; hits were
+// zeroed before it ran.  A thread reads at most above / 32 + 2 words, and the
+// threads of a warp read neighbouring reads' words.
+__global__ void __launch_bounds__(256) short_read_hits_kernel(const uint32_t* __restrict__ bits,
+                                                              const uint64_t* __restrict__ off,
+                                                              uint64_t n_reads, uint64_t seq_len,
+                                                              uint32_t above,
+                                                              uint32_t* __restrict__ hits) {
+  const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_reads) return;
+  uint64_t a = __ldg(off + r), b = __ldg(off + r + 1);
+  a = a < seq_len ? a : seq_len;
+  b = b < seq_len ? b : seq_len;
+  if (b <= a || b - a > above) return;
+  const uint64_t w0 = a >> 5, w1 = (b - 1) >> 5;
+  uint32_t cnt = 0;
+  for (uint64_t w = w0; w <= w1; ++w) {
+    uint32_t x = __ldg(bits + w);
+    if (w == w0) x &= 0xFFFFFFFFu << (uint32_t)(a & 31u);
+    if (w == w1) x &= 0xFFFFFFFFu >> (31u - (uint32_t)((b - 1) & 31u));
+    cnt += __popc(x);
+  }
+  hits[r] = cnt;
+}
+
+uint32_t hits_above_for(uint64_t positions, bool both_outputs) {
+  if (!both_outputs) return 0u;
+  uint64_t min_positions = kHitsPassMinPositions;
+  const char* env = getenv("SBF_HITS_PASS_MIN_POSITIONS");
+  if (env && *env) min_positions = strtoull(env, nullptr, 10);
+  return positions >= min_positions ? kShortReadMax : 0u;
+}
+
+cudaError_t short_read_hits(const uint32_t* bits, const uint64_t* off, uint64_t n_reads,
+                            uint64_t seq_len, uint32_t above, uint32_t* hits, cudaStream_t st) {
+  if (above == 0 || n_reads == 0 || !bits || !hits) return cudaSuccess;
+  const uint64_t blocks = (n_reads + 255) / 256;
+  short_read_hits_kernel<<<(unsigned)blocks, 256, 0, st>>>(bits, off, n_reads, seq_len, above, hits);
+  return cudaGetLastError();
+}
+
 }  // namespace fused
 
 bool fused_supported(const Geom& g) {
@@ -93,7 +139,10 @@ cudaError_t fused_query(const Geom& g, const uint8_t* seq, uint64_t seq_len, con
   }
   if (seq_len == 0 || n_reads == 0) return cudaSuccess;
   fused::Params P = fused::single(g, seq, seq_len, off, n_reads, bits, hits, stats);
-  return fused::run(P, false, st);
+  // with both outputs, short reads' hits come from the answer words afterwards
+  P.hits_above = fused::hits_above_for(seq_len, bits && hits);
+  if ((e = fused::run(P, false, st)) != cudaSuccess) return e;
+  return fused::short_read_hits(bits, off, n_reads, seq_len, P.hits_above, hits, st);
 }
 
 }  // namespace sbf

@@ -245,6 +245,8 @@ struct Params {
   uint32_t chunk;         // iterations per dynamically claimed work item
   uint32_t grid_blocks;   // blocks to launch (0: enough for the work, capped at full occupancy)
   uint32_t big;           // a segment's filter has kTmaMinBytes or more (query: BULK kernels)
+  uint32_t hits_above;    // query: the kernel counts hits of reads longer than this (0: of every
+                          // read); shorter reads are counted afterwards from the answer words
 };
 
 template <int SC, int H, int B, bool KEY64>
@@ -985,8 +987,22 @@ __device__ __forceinline__ bool run_range(WarpSmem<slot_cap<W, INSERT>(), H, B, 
           }
         }
       }
-      // per-read hit counts from prefix popcounts of the answer words
-      if (seg.hits) {
+      // per-read hit counts from prefix popcounts of the answer words.
+      // Batch 0 reuses the prefetched read ends: read q = r_cur + lane spans
+      // [end of q-1, end of q).  Reads of at most P.hits_above positions are
+      // left to the short-read pass; an iteration that holds no other read
+      // (and no second batch) skips the counting.
+      uint64_t q0 = r_cur;
+      uint64_t re = e_batch;
+      uint64_t rs = __shfl_up_sync(kFull, re, 1);
+      if (lane == 0) rs = r_cur_start;
+      const uint64_t ha = P.hits_above;
+      bool count_here = seg.hits != nullptr;
+      if (count_here && ha != 0) {
+        const bool mine = q0 + lane < n_reads && rs < own_hi && re > p0 && re - rs > ha;
+        count_here = __any_sync(kFull, mine) || __all_sync(kFull, re < own_hi);
+      }
+      if (count_here) {
         __syncwarp();
         const uint32_t pc = lane < 16 ? __popc(S.k_w[lane]) : 0u;
         uint32_t incl = pc;
@@ -1005,15 +1021,9 @@ __device__ __forceinline__ bool run_range(WarpSmem<slot_cap<W, INSERT>(), H, B, 
           const uint32_t w = x >> 5, b = x & 31u;
           return S.pref_w[w] + (b ? __popc(S.k_w[w] & (0xFFFFFFFFu >> (32u - b))) : 0u);
         };
-        // batch 0 reuses the prefetched read ends: read q = r_cur + lane spans
-        // [end of q-1, end of q)
-        uint64_t q0 = r_cur;
-        uint64_t re = e_batch;
-        uint64_t rs = __shfl_up_sync(kFull, re, 1);
-        if (lane == 0) rs = r_cur_start;
         while (true) {
           const uint64_t q = q0 + lane;
-          if (q < n_reads && rs < own_hi && re > p0) {
+          if (q < n_reads && rs < own_hi && re > p0 && (ha == 0 || re - rs > ha)) {
             const uint64_t a = rs > p0 ? rs - p0 : 0;
             const uint64_t b = (re < own_hi ? re : own_hi) - p0;
             if (b > a) {
@@ -1191,6 +1201,23 @@ inline bool is_big(const Geom& g) {
 
 // Launch a prepared parameter block (dispatch over the compiled grid).
 cudaError_t launch_params(const Params& P, bool insert, cudaStream_t st);
+// Reads of at most this many positions have their hits counted from the
+// answer words by short_read_hits when a query writes both outputs.
+constexpr uint32_t kShortReadMax = 2048;
+// Below this many start positions per launch the query kernel counts every
+// read itself: the second launch's fixed cost (about 10-20 us) exceeds what
+// it saves (about 0.3 ns per position).
+constexpr uint64_t kHitsPassMinPositions = 1ull << 26;
+// hits_above for a query launch over `positions` start positions that writes
+// both outputs (0 otherwise).  SBF_HITS_PASS_MIN_POSITIONS overrides the
+// minimum (the tests set 0 to run the pass on small inputs).
+uint32_t hits_above_for(uint64_t positions, bool both_outputs);
+// The short-read pass of a query launched with hits_above = `above`: hits of
+// the reads of at most `above` positions, from the answer words `bits`
+// (indexed by position; one thread per read).  Launch it after the query
+// kernel on the same stream; it does nothing when above is 0.
+cudaError_t short_read_hits(const uint32_t* bits, const uint64_t* off, uint64_t n_reads,
+                            uint64_t seq_len, uint32_t above, uint32_t* hits, cudaStream_t st);
 // Start positions covered by one iteration for these parameters.
 int advance_of(const Geom& g);
 

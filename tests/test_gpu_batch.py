@@ -48,9 +48,18 @@ def _filters(params, bits):
     return [SuperBloomFilter(k, m, s, H, b, shard_bits=B, canonical=canon) for b in bits]
 
 
+@pytest.mark.parametrize("hits_pass", [True, False], ids=["hits_pass", "hits_in_kernel"])
 @pytest.mark.parametrize("params", PARAMS, ids=lambda p: "_".join(map(str, p)))
-def test_batched_insert_and_query_match_oracle(params, workload):
+def test_batched_insert_and_query_match_oracle(params, workload, hits_pass, monkeypatch):
+    """hits_pass: the persistent launch leaves reads of at most 2048 positions
+    to the short-read hit pass (forced onto this small batch by its knob);
+    one launch per filter counts every read in the kernel either way."""
     from paper_2606_24417_gb300.sbf import BATCH_FUSED, BATCH_GRAPH, BATCH_PER_FILTER, FilterBatch
+
+    if hits_pass:
+        monkeypatch.setenv("SBF_HITS_PASS_MIN_POSITIONS", "0")
+    else:
+        monkeypatch.delenv("SBF_HITS_PASS_MIN_POSITIONS", raising=False)
 
     w = workload
     k, m, s, H, B, canon = params

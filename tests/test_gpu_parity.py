@@ -181,6 +181,45 @@ def test_many_short_reads(params):
     check_insert_query(params, seq, off, seq, off)
 
 
+@pytest.mark.parametrize("params", [(31, 16, 28, 4, 1 << 22, 512, True),   # fused kernels
+                                    (31, 20, 24, 8, 1 << 22, 256, True)],  # fused, 64-bit keys
+                         ids=lambda p: "_".join(map(str, p)))
+@pytest.mark.parametrize("hits_pass", [True, False], ids=["pass", "in_kernel"])
+def test_read_hits_at_the_short_read_limit(params, hits_pass, monkeypatch):
+    """With both outputs on a large enough launch, the query kernel counts
+    hits of reads longer than 2048 positions and a second pass counts the
+    rest from the answer words; otherwise the kernel counts every read.
+    Reads of lengths around the limit, mixed with short, empty and long reads
+    in a shuffled order, give the oracle's hits both ways, on the device and
+    the host paths (the pass is forced onto this small input by its knob)."""
+    if hits_pass:
+        monkeypatch.setenv("SBF_HITS_PASS_MIN_POSITIONS", "0")
+    else:
+        monkeypatch.delenv("SBF_HITS_PASS_MIN_POSITIONS", raising=False)
+    genome = synth.uniform_dna(400_000, 71)
+    lens = [0, 1, 30, 31, 32, 150, 2046, 2047, 2048, 2049, 2050, 2079, 2080, 4096, 20_000,
+            150, 151, 2048, 0, 2049, 60_000] * 6
+    lens = np.asarray(lens, dtype=np.int64)[synth.randint(72, 1, len(lens), 0, 1 << 30).argsort()]
+    src = synth.randint(73, 1, lens.size, 0, genome.size - 60_001)
+    reads = []
+    for i, L in enumerate(lens):
+        r = genome[src[i]:src[i] + L].copy() if i % 3 else synth.uniform_dna(int(L), 74 + i)
+        reads.append(r)
+    seq, off = synth.concat(reads)
+    f, o = check_insert_query(params, genome, np.array([0, genome.size], np.uint64), seq, off)
+    ob, oh = o.query(seq, off)
+    assert int(oh[lens > 2048].sum()) > 0 and int(oh[(lens > 0) & (lens <= 2048)].sum()) > 0
+    qb, _ = f.query(dev(seq), dev_off(off), want_hits=False)
+    _, qh = f.query(dev(seq), dev_off(off), want_bits=False)
+    assert np.array_equal(u32(qb), ob) and np.array_equal(u32(qh), oh)
+    monkeypatch.setenv("SBF_HOST_CHUNK_BYTES", "50000")   # chunk seams between long reads
+    hb, hh = f.query_host(seq, off)
+    assert np.array_equal(hb, ob) and np.array_equal(hh, oh)
+    _, hh2 = f.query_host(seq, off, want_bits=False)
+    assert np.array_equal(hh2, oh)
+    f.close()
+
+
 def test_insert_order_and_repeats_on_gpu():
     params = (31, 16, 28, 4, 1 << 21, 512, True)
     seq, off = ragged_reads(3000, 21)
@@ -222,8 +261,8 @@ def test_host_path_matches_device(monkeypatch, params):
     ph = torch.empty(hh.size, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
     f.query_host(q_seq, q_off, bits=pb, hits=ph)
     assert np.array_equal(pb, ob) and np.array_equal(ph, oh)
-    # pinned inputs: the fused kernels read them in place over the link
-    # instead of copying chunks in; same answers, same filter
+    # pinned inputs (copied in by chunks like pageable ones, without the
+    # staging step): same answers, same filter
     pq = torch.from_numpy(q_seq).pin_memory().numpy()
     po = torch.from_numpy(q_off.view(np.int64)).pin_memory().numpy().view(np.uint64)
     f.query_host(pq, po, bits=pb, hits=ph)
