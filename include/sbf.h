@@ -186,9 +186,10 @@ int sbf_or_reduce_device(uint64_t* d_out, const uint64_t* d_in, uint64_t n_words
  * sbf_query_seqs: d_kmer_bits: ceil(seq_len/32) uint32 (may be NULL);
  *   d_read_hits: n_reads uint32 (may be NULL).  Both are overwritten.
  *   d_read_hits[r] is the number of set answer bits at read r's start
- *   positions.  With both outputs on the fused kernels, reads of at most
- *   2048 positions are counted from the answer words by a second small
- *   kernel on the same stream; longer reads are counted in the query kernel.
+ *   positions.  With both outputs on the fused kernels and at least 2^26
+ *   start positions, reads of at most 2048 positions are counted from the
+ *   answer words by a second small kernel on the same stream; longer reads
+ *   (and every read otherwise) are counted in the query kernel.
  * sbf_query_seqs_ex: as sbf_query_seqs, and if d_stats != NULL adds into
  *   d_stats[0] the number of valid k-mers, d_stats[1] the number of
  *   super-k-mer runs (maximal spans of consecutive valid k-mers of one read

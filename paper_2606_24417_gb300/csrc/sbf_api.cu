@@ -552,11 +552,12 @@ int host_run_fused(sbf_filter* f, bool is_query, const uint8_t* h_seq, const uin
     P.chunk = 1;
     P.grid_blocks = 0;
     P.big = fused::is_big(f->geom) ? 1u : 0u;
-    P.hits_above = fused::hits_above_for(len, want_bits && want_hits);
-    if ((e = fused::launch_params(P, !is_query, st)) != cudaSuccess ||
-        (is_query && (e = fused::short_read_hits(sg.bits, sg.off, nr, sg.seq_len, P.hits_above,
-                                                 sg.hits, st)) != cudaSuccess))
-      return cuda_fail(e, "host path launch");
+    // hits of every read are counted in the kernel: a short-read pass after
+    // it could not start before the other stream's query kernel (which holds
+    // every SM) ended, and the chunk's copies queued behind it would stop
+    // overlapping the kernels (measured: 20.6 -> 25.1 ms for 20M reads)
+    P.hits_above = 0;
+    if ((e = fused::launch_params(P, !is_query, st)) != cudaSuccess) return cuda_fail(e, "host path launch");
     uint32_t* hits_dst = stage_hits ? f->host_stage_hits[b] : h_hits + c.r0;
     uint32_t* bits_dst = stage_bits ? f->host_stage_bits[b] + 1 : h_bits + c.a / 32 + 1;
     if (stage_bits || stage_hits) pending[b] = (int64_t)ci;

@@ -81,6 +81,8 @@ __global__ void __launch_bounds__(256) short_read_hits_kernel(const uint32_t* __
   hits[r] = cnt;
 }
 
+// The pass's blocks wait for free SMs, so paths that overlap query kernels
+// on several streams (the host-input path) count every read in the kernel.
 uint32_t hits_above_for(uint64_t positions, bool both_outputs) {
   if (!both_outputs) return 0u;
   uint64_t min_positions = kHitsPassMinPositions;

@@ -190,8 +190,9 @@ def test_read_hits_at_the_short_read_limit(params, hits_pass, monkeypatch):
     hits of reads longer than 2048 positions and a second pass counts the
     rest from the answer words; otherwise the kernel counts every read.
     Reads of lengths around the limit, mixed with short, empty and long reads
-    in a shuffled order, give the oracle's hits both ways, on the device and
-    the host paths (the pass is forced onto this small input by its knob)."""
+    in a shuffled order, give the oracle's hits both ways on the device path
+    (the pass is forced onto this small input by its knob), and on the host
+    path, which counts every read in the kernel."""
     if hits_pass:
         monkeypatch.setenv("SBF_HITS_PASS_MIN_POSITIONS", "0")
     else:
