@@ -260,10 +260,8 @@ struct alignas(16) WarpSmem {
   uint32_t shard[SC * L::SLOT];          // shard copies (query) or masks (insert)
   SlotT slot_x[512];
   Pack hs[kLanePos * kHsStride];         // s-mer bit-address packs, [j][lane]
-  uint16_t end_slot[512];                // slot of each run end
   uint16_t slot_of[kLanePos * 34];       // slot of each valid position, [j][lane]
-  uint16_t end_list[512];                // run-end positions
-  uint16_t slot_head[512];               // run-head position of each slot
+  uint16_t end_list[512];                // run-end positions (end i closes slot i)
   uint32_t fwd[kStage];                  // staged 2-bit words
   uint32_t rcw[kStage];                  // their reverse complements
   uint32_t bad[kStage];                  // 16-bit invalid masks
@@ -696,14 +694,9 @@ __device__ __forceinline__ bool run_range(WarpSmem<slot_cap<W, INSERT>(), H, B, 
         if ((slot16 >> j) & 1u) {
           ++sl;
           S.slot_x[sl] = (typename Sm::SlotT)mk[j];
-          S.slot_head[sl] = (uint16_t)t;
         }
         if (kFastOwn || ((valid16 >> j) & 1u)) S.slot_of[j * 34 + lane] = (uint16_t)sl;
-        if ((end16 >> j) & 1u) {
-          S.end_list[en] = (uint16_t)t;
-          S.end_slot[en] = (uint16_t)sl;
-          ++en;
-        }
+        if ((end16 >> j) & 1u) S.end_list[en++] = (uint16_t)t;
       }
     }
     reinterpret_cast<uint16_t*>(S.valid_w)[lane] = (uint16_t)valid16;
@@ -913,10 +906,15 @@ __device__ __forceinline__ bool run_range(WarpSmem<slot_cap<W, INSERT>(), H, B, 
 
     // extra pairs after each run end e: (e+d, shard(e)), d = 1..z.  A failure
     // at d kills the run's k-mers [max(e+d-z, head), e]; the smallest failing
-    // d gives the largest range, so testing stops there.
+    // d gives the largest range, so testing stops there.  Every slot holds
+    // one run piece with one end, and slots and ends are both numbered in
+    // position order, so end i belongs to slot i.  Every valid position
+    // between run i-1's end and run i's head would be in a run, so none is:
+    // the position after end i-1 serves as the head (the positions it adds
+    // to a kill range are invalid, and answers keep valid positions only).
     for (uint32_t ei = lane; ei < total_ends; ei += 32) {
       const uint32_t e = S.end_list[ei];
-      const uint32_t slot = S.end_slot[ei];
+      const uint32_t slot = ei;
       if constexpr (INSERT) {
         for (int d = 1; d <= z; ++d) {
           const uint32_t t = e + d;
@@ -933,7 +931,7 @@ __device__ __forceinline__ bool run_range(WarpSmem<slot_cap<W, INSERT>(), H, B, 
         }
         if (fail) {
           int lo = (int)e + fail - z;
-          const int hd = S.slot_head[slot];
+          const int hd = ei > 0 ? (int)S.end_list[ei - 1] + 1 : 0;
           if (lo < hd) lo = hd;
           const uint32_t w1 = (uint32_t)lo >> 5, w2 = e >> 5;
           const uint32_t bl = (uint32_t)lo & 31u, bh = e & 31u;
