@@ -48,13 +48,14 @@ constexpr int kWarps = 4;           // warps per block
 constexpr int kThreads = 32 * kWarps;
 constexpr int kSlotCap = 64;        // runs per iteration with a shard copy in shared memory
 // Windows of 12 or less (m = 20 at k = 31) give about 2/(w+1) * 496 = 76 runs
-// per iteration, more than 64 slots, and an insert's runs past the last slot
-// set their bits with global atomics.  Inserts with such windows keep 96
-// slots in shared memory (m = 20, H = 8 inserts 3.6x faster on 512-bit shards,
-// 2.3x on 256-bit); queries keep 64, because their fallback is a plain load
-// and the larger array costs the 512-bit-shard kernels a resident block.
-template <int W, bool INSERT>
-constexpr int slot_cap() { return (INSERT && W <= 12) ? 96 : kSlotCap; }
+// per iteration, more than 64 slots; runs past the last slot set their bits
+// with global atomics (insert) or test them with global loads (query).
+// Inserts with such windows keep 96 slots in shared memory (m = 20, H = 8
+// inserts 3.6x faster on 512-bit shards, 2.3x on 256-bit), and so do the
+// queries on 512-bit shards, which run 3 blocks per SM either way; the
+// 256-bit-shard queries (4 blocks per SM) would lose a block to the array.
+template <int W, bool INSERT, int B>
+constexpr int slot_cap() { return (W <= 12 && (INSERT || B == 512)) ? 96 : kSlotCap; }
 constexpr int kStage = 34;          // staged 16-base words per iteration (544 bases)
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
@@ -393,7 +394,7 @@ __device__ bool prev_kmer_key(const Geom& g, const uint8_t* seq, uint64_t seq_le
 // wait for shard copies ran out (the filter's status word is set).  BULK:
 // the kernel variant for launches with a filter of kTmaMinBytes or more.
 template <int W, int H, int B, bool KEY64, bool INSERT, bool BULK>
-__device__ __forceinline__ bool run_range(WarpSmem<slot_cap<W, INSERT>(), H, B, KEY64>& S,
+__device__ __forceinline__ bool run_range(WarpSmem<slot_cap<W, INSERT, B>(), H, B, KEY64>& S,
                                           const Params& P,
                                           const Segment& seg, uint64_t it0, uint64_t it1,
                                           int lane, unsigned long long& st_valid,
@@ -402,16 +403,17 @@ __device__ __forceinline__ bool run_range(WarpSmem<slot_cap<W, INSERT>(), H, B, 
   using L = Layout<H, B>;
   using Pack = typename L::Pack;
   using KeyT = typename std::conditional<KEY64, uint64_t, uint32_t>::type;
-  using Sm = WarpSmem<slot_cap<W, INSERT>(), H, B, KEY64>;
+  using Sm = WarpSmem<slot_cap<W, INSERT, B>(), H, B, KEY64>;
   constexpr int U = Shape<W>::kUseful;
   constexpr int ADV = Shape<W>::kAdvance;
   constexpr int HS = Sm::kHsStride;
-  constexpr int SC = slot_cap<W, INSERT>();  // runs of an iteration with a slot in shared memory
+  constexpr int SC = slot_cap<W, INSERT, B>();  // runs of an iteration with a slot in shared memory
   // Queries test own pairs without masks or a global fallback when all runs of
   // an iteration have a slot.  That pays where the runs (about 2/(W+1) of
-  // the 496 positions) usually fit the 64 slots, W >= 16; at W = 12 they
-  // average 76, and the second loop only adds code (2-5% slower there).
-  constexpr bool kFastOwn = !INSERT && W > 12;
+  // the 496 positions) usually fit the slots: W >= 16 with 64 slots, W = 12
+  // with 96; at W = 12 with 64 slots (average 76 runs) the second loop only
+  // adds code (2-5% slower there).
+  constexpr bool kFastOwn = !INSERT && (W > 12 || SC > kSlotCap);
   Geom g = P.g;
   g.words = seg.words;
   g.n_shards = seg.n_shards;
@@ -844,11 +846,16 @@ __device__ __forceinline__ bool run_range(WarpSmem<slot_cap<W, INSERT>(), H, B, 
       if (total_slots <= (uint32_t)SC) {
         // every run has a shared copy; an invalid position's slot entry
         // (written, but of no run) is reduced into range
-        static_assert((SC & (SC - 1)) == 0, "query slot count is a power of two");
+        constexpr bool kPow2 = (SC & (SC - 1)) == 0;
+        constexpr uint32_t kMask = kPow2 ? (uint32_t)(SC - 1) : 0xFFFFFFFFu;
 #pragma unroll 4
         for (int pass = 0; pass < 16; pass += 2) {
-          const uint32_t sla = S.slot_of[so_i0 + 2 * pass] & (uint32_t)(SC - 1);
-          const uint32_t slb = S.slot_of[so_i0 + 2 * pass + 2] & (uint32_t)(SC - 1);
+          uint32_t sla = S.slot_of[so_i0 + 2 * pass] & kMask;
+          uint32_t slb = S.slot_of[so_i0 + 2 * pass + 2] & kMask;
+          if constexpr (!kPow2) {
+            sla = sla < (uint32_t)SC ? sla : 0u;
+            slb = slb < (uint32_t)SC ? slb : 0u;
+          }
           const unsigned own_a = __ballot_sync(
               kFull, test_slot<H, B>(&S.shard[sla * L::SLOT], S.hs[hs_i0 + 2 * pass]) != 0u);
           const unsigned own_b = __ballot_sync(
@@ -1085,7 +1092,7 @@ constexpr int min_blocks() {
 template <int W, int H, int B, bool KEY64, bool INSERT, bool BULK>
 __global__ void __launch_bounds__(kThreads, min_blocks<KEY64, INSERT, B>()) fused_kernel(Params P) {
   static_assert(!(INSERT && BULK), "bulk shard copies are a query variant");
-  using Sm = WarpSmem<slot_cap<W, INSERT>(), H, B, KEY64>;
+  using Sm = WarpSmem<slot_cap<W, INSERT, B>(), H, B, KEY64>;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   Sm& S = reinterpret_cast<Sm*>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
@@ -1172,7 +1179,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<KEY64, INSERT, B>()) fuse
 template <int W, int H, int B, bool KEY64, bool INSERT, bool BULK = false>
 cudaError_t launch(const Params& P, cudaStream_t st) {
   auto kern = fused_kernel<W, H, B, KEY64, INSERT, BULK>;
-  constexpr size_t smem = sizeof(WarpSmem<slot_cap<W, INSERT>(), H, B, KEY64>) * kWarps;
+  constexpr size_t smem = sizeof(WarpSmem<slot_cap<W, INSERT, B>(), H, B, KEY64>) * kWarps;
   static int blocks_per_sm = 0;  // per instantiation; same on every GB300
   if (blocks_per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

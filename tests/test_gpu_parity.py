@@ -343,8 +343,8 @@ def test_fused_matches_generic_large(params, monkeypatch):
                          ids=lambda p: "_".join(map(str, p)))
 def test_large_filter_bulk_copies(params):
     """Filters of 1 GiB load part of their shards with TMA bulk copies on an
-    mbarrier (slots 32..63 of an iteration): words, bits and hits equal the
-    oracle's, and no wait ran out."""
+    mbarrier (slots from 32 on of an iteration; up to 95 for the w = 12
+    kernel): words, bits and hits equal the oracle's, and no wait ran out."""
     g = synth.bacterial_genome(3_000_000, seed=31)
     goff = np.array([0, g.size], dtype=np.uint64)
     q, qoff = ragged_reads(60_000, 32, genome=g)
